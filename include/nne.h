@@ -1,0 +1,184 @@
+/*
+ * libnne -- C ABI of the GB300 (sm_103a) hot path of non-zero noise
+ * extrapolation (NZNE, arXiv 2501.13237).
+ *
+ * What the library computes (paper sections in brackets):
+ *   - a vectorised density operator |rho>> stored as an MPS with local
+ *     dimension 4 per qubit, |i><j| -> |(i,j)>>, s = 2 i + j        [Sec. 2.1.1]
+ *   - noisy circuit evolution: each two-qubit gate U is post-composed with a
+ *     channel C (U -> C o U) and applied as one 16x16 superoperator G;
+ *     after each gate the state is replaced by the closest bond-chi state of
+ *     Frobenius norm 1; the partial fidelity f_l of that step is recorded and
+ *     F = prod f_l is accumulated                              [Secs. 2.1.2, 2.2.1]
+ *   - Pauli expectation values <P> = Tr(P rho)/Tr(rho) read off by an exact
+ *     contraction of the network                               [Sec. 2.2.3]
+ *   - the extrapolation of <O>_lambda across noise levels to a target
+ *     lambda* (weighted log-linear, three-parameter exponential, or
+ *     polynomial fit)                                          [Sec. 2.2.3 (B), App. B.2]
+ *
+ * Conventions shared by every entry point
+ *   - Complex numbers are (re, im) pairs of float (NNE_C64) or double
+ *     (NNE_C128), interleaved.
+ *   - A state holds n_inst independent instances (normally one per noise
+ *     level lambda) of the same circuit: same n, same chi, same gate
+ *     positions, per-instance superoperators.
+ *   - Site tensor k of an instance is M[a][s][b] (row-major, b fastest) with
+ *     shape (dims[k], 4, dims[k+1]); dims[0] = dims[n] = 1.
+ *   - Superoperators G are 16x16 complex128, row-major, row index
+ *     4*s1' + s2', column index 4*s1 + s2, qubit q (s1) the left qubit.
+ *   - Pauli codes: 0 = I, 1 = X, 2 = Y, 3 = Z.
+ *   - Host pointers are owned by the caller and must stay valid until the
+ *     call returns; device pointers are owned by the caller and must stay
+ *     valid until the work enqueued by the call has completed on the
+ *     context's stream.  The library owns all state and workspace memory.
+ *   - Errors are returned as nne_status; nothing throws or aborts across the
+ *     ABI.  nne_last_error() gives a one-line description of the most recent
+ *     failure on the calling thread.  Calls on one context are not
+ *     thread-safe (a server serialises them itself).
+ */
+#ifndef NNE_H
+#define NNE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nne_status;
+#define NNE_OK 0
+#define NNE_PENDING 1
+#define NNE_ERR_ARG (-1)
+#define NNE_ERR_OOM (-2)
+#define NNE_ERR_CUDA (-3)
+#define NNE_ERR_NOCONV (-4)
+#define NNE_ERR_TIMEOUT (-5)
+#define NNE_ERR_NOFIT (-6)
+#define NNE_ERR_UNIMPL (-7)
+
+typedef enum { NNE_C64 = 0, NNE_C128 = 1 } nne_dtype;
+
+/* Truncation algorithm of a gate step.
+ * NNE_TRUNC_EXACT: eigenvectors of the full (4 chi_l)^2 Gram matrix X X^dagger
+ *   (or X^dagger X), i.e. the exact best rank-chi approximation (Eckart-Young).
+ * NNE_TRUNC_RSVD: randomized range finder with q power iterations and a
+ *   Rayleigh-Ritz step on a (chi + p)-dimensional sketch (Halko, Martinsson &
+ *   Tropp 2011); the sketch matrix is an input (nne_set_sketch).  Equals
+ *   NNE_TRUNC_EXACT whenever chi + p covers the rank bound of the gate. */
+typedef enum { NNE_TRUNC_EXACT = 0, NNE_TRUNC_RSVD = 1 } nne_trunc;
+
+/* Fit methods of nne_extrapolate. */
+typedef enum { NNE_FIT_POLY = 0, NNE_FIT_EXP_LOGLIN = 1, NNE_FIT_EXP3 = 2 } nne_fit;
+
+typedef struct nne_ctx nne_ctx;
+typedef struct nne_state nne_state;
+
+/* Context: one CUDA device and one stream.
+ *   device           CUDA ordinal made current by every call on this context.
+ *   cuda_stream      cudaStream_t (NULL = the legacy default stream).
+ *   hbm_budget_bytes cap on the memory states created on this context may
+ *                    allocate (0 = no cap); exceeding it gives NNE_ERR_OOM. */
+nne_status nne_ctx_create(int device, void* cuda_stream, size_t hbm_budget_bytes, nne_ctx** out);
+void nne_ctx_destroy(nne_ctx* ctx);
+/* Bytes currently allocated by states of this context. */
+size_t nne_ctx_bytes_in_use(const nne_ctx* ctx);
+const char* nne_last_error(void);
+
+/* a1 -- fused gate+channel superoperators (Sec. 2.2.1 eq. U -> C o U; App. C.2.1).
+ * G[i][g] = S_depol1 S_dephase S_ampdamp S_depol2 (U_g (x) conj(U_g)) for
+ * instance i and gate g, where each S is sum_K K (x) conj(K) of the channel
+ * at the strengths rates[i] = (p_depol2, gamma, p_dephase, p_depol1):
+ *   depol2   K0 = sqrt(1 - 15p/16) I, K_ab = sqrt(p/16) sigma_a sigma_b
+ *            (rho -> (1-p) rho + p I/4; App. C.2.1)
+ *   ampdamp  K0 = diag(1, sqrt(1-gamma)), K1 = sqrt(gamma)|0><1|, on both qubits
+ *   dephase  sqrt(1-p) I, sqrt(p) Z on both qubits
+ *   depol1   sqrt(1-p) I, sqrt(p/3){X,Y,Z} on both qubits
+ * U     host, n_gates x 4 x 4 complex128 (row-major, basis |b_q b_{q+1}>, b_q
+ *       the more significant bit).
+ * rates host, n_inst x 4 doubles; every strength in [0, 1] (depol2 <= 16/15).
+ * G_out device, n_inst x n_gates x 256 complex128.
+ * Computed in float64 on the device; enqueued on the context stream. */
+nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_inst,
+                              const double* rates, void* G_out);
+
+/* State creation: n_inst instances of the product state |b><b| (Sec. 2.1.2:
+ * the initial state is a product state), bond dimensions 1, orthogonality
+ * centre on site 0, log-norm and log-fidelity 0.
+ *   n_qubits >= 2, chi >= 1, n_inst >= 1; init_bits host uint8[n] (NULL = all 0).
+ * Device memory is sized for bond capacities min(chi, 4^k, 4^(n-k)). */
+nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne_dtype dtype,
+                            nne_trunc trunc, const uint8_t* init_bits, nne_state** out);
+void nne_destroy_state(nne_state* st);
+
+/* Sketch matrix of NNE_TRUNC_RSVD: host complex (same precision as the state)
+ * of rows x cols, rows >= 4*chi, cols = chi + oversampling; power_iters >= 0. */
+nne_status nne_set_sketch(nne_state* st, const void* omega, int rows, int cols, int power_iters);
+
+/* a2-a6 -- one layer of gates (Sec. 2.1.2 "Approximate emulation").
+ * For each gate g in array order, on sites (q, q+1), q = left_qubit[g]:
+ *   move the orthogonality centre to q (direction +1) or q+1 (direction -1)
+ *   by QR / LQ steps; form theta = M_q M_{q+1} and theta' = G theta over
+ *   (s1, s2); truncate X = theta' ((4 chi_l) x (4 chi_r)) to rank
+ *   r = min(chi, 4 chi_l, 4 chi_r); keep the isometric factor on q (+1) or
+ *   q+1 (-1) and the centre on the other site; normalise the centre to
+ *   Frobenius norm 1 and add log|centre| to log_norm and
+ *   log f_l = log(sum_{i<=r} s_i^2 / sum s_i^2) to log F.
+ * left_qubit host int[n_gates], 0 <= q <= n-2.
+ * G device, n_inst x n_gates x 256 complex128 (gate g of instance i at
+ *   G + (i * n_gates + g) * 256).
+ * Enqueued on the context stream; device-side failures surface at the next
+ * nne_sync / nne_expect / nne_state_info. */
+nne_status nne_apply_layer(nne_state* st, int n_gates, const int* left_qubit, const void* G,
+                           int direction);
+
+/* Canonical compression sweep to bond dimension chi_new (<= current chi):
+ * centre to site 0, then left to right keep min(chi_new, .) singular
+ * triplets per bond, normalise, accumulate log f per bond.  log_fid_out
+ * (host double[n_inst] or NULL) receives the log F added by this call. */
+nne_status nne_truncate(nne_state* st, int chi_new, double* log_fid_out);
+
+/* a7 -- <P> = Tr(P rho)/Tr(rho) for each Pauli string (Sec. 2.2.3; exact
+ * contraction of the network).  paulis host uint8 n_obs x n; re_out/im_out
+ * host double n_inst x n_obs; log_fid_out host double[n_inst] or NULL
+ * (log F of each instance).  Synchronises the context stream. */
+nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* re_out,
+                      double* im_out, double* log_fid_out);
+
+/* a8 -- noise extrapolation to lambda_star (Sec. 2.2.3 (B), App. B.2), FP64
+ * on the device, one thread per observable.
+ *   lambdas host double[n_lambda]; values host double n_lambda x n_obs;
+ *   log_fid host double[n_lambda] (log F per level) or NULL (= 0);
+ *   y_zero  host double[n_obs] (lambda = 0 values, the sign reference of
+ *           criterion 3) or NULL (reference = smallest lambda);
+ *   method NNE_FIT_POLY (degree >= 1), NNE_FIT_EXP_LOGLIN (criteria 2-3,
+ *          weights F^2 exp(-20|lambda*-lambda|/d), fallback to EXP3 when
+ *          fewer than two points survive), NNE_FIT_EXP3 (a e^{-b lambda} + c);
+ *   out host double[n_obs]; per_obs_status host int32[n_obs]: NNE_OK or
+ *          NNE_ERR_NOFIT (then out = the value at lambda* if lambda* was
+ *          emulated, else NaN -- the paper's final fallback).
+ * Returns NNE_OK unless an argument or CUDA call fails. */
+nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, const double* values,
+                           const double* log_fid, int n_obs, int method, int degree,
+                           double lambda_star, const double* y_zero, double* out,
+                           int32_t* per_obs_status);
+
+/* Wait for the state's enqueued work; returns the first device-side error. */
+nne_status nne_sync(nne_state* st);
+
+/* Host view of a state: dims_out int[n+1], centre_out, log_norm_out /
+ * log_fid_out double[n_inst] (any may be NULL).  Synchronises. */
+nne_status nne_state_info(nne_state* st, int* dims_out, int* centre_out, double* log_norm_out,
+                          double* log_fid_out);
+/* Copy site k of instance inst to/from host memory (shape dims[k] x 4 x dims[k+1],
+ * element size 8 or 16 bytes).  nne_state_write_site sets the bond dims of
+ * site k to (dl, dr); the caller keeps neighbouring sites consistent and
+ * declares the orthogonality centre with nne_state_set_centre.  Synchronises. */
+nne_status nne_state_read_site(nne_state* st, int inst, int k, void* host_out, size_t cap_bytes);
+nne_status nne_state_write_site(nne_state* st, int inst, int k, int dl, int dr, const void* host_in);
+nne_status nne_state_set_centre(nne_state* st, int centre);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNE_H */

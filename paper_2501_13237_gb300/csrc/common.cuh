@@ -1,0 +1,70 @@
+// Shared device/host helpers for libnne (complex arithmetic, launch checks).
+#pragma once
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/nne.h"
+
+namespace nne {
+
+template <typename R>
+struct __align__(2 * sizeof(R)) cx {
+  R re, im;
+};
+
+template <typename R> __host__ __device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> z; z.re = a; z.im = b; return z; }
+template <typename R> __host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R> __host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R> __host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R> __host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk(s * a.re, s * a.im); }
+template <typename R> __host__ __device__ __forceinline__ cx<R> conj(cx<R> a) { return mk(a.re, -a.im); }
+template <typename R> __host__ __device__ __forceinline__ R norm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// a += b * c
+template <typename R> __host__ __device__ __forceinline__ void fma_(cx<R>& a, cx<R> b, cx<R> c) {
+  a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+  a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+// a += conj(b) * c
+template <typename R> __host__ __device__ __forceinline__ void fmac_(cx<R>& a, cx<R> b, cx<R> c) {
+  a.re = fma(b.re, c.re, fma(b.im, c.im, a.re));
+  a.im = fma(b.re, c.im, fma(-b.im, c.re, a.im));
+}
+template <typename R> __device__ __forceinline__ cx<R> shfl_xor(cx<R> v, int m) {
+  return mk(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
+}
+template <typename R> __device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
+  for (int m = 16; m > 0; m >>= 1) v = v + shfl_xor(v, m);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_sum_r(T v) {
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// Matrix operation flags for the batched complex GEMM.
+enum Op { OP_N = 0, OP_C = 1 };
+
+// Strided batch descriptor: matrix b of a batch starts at ptr + b * stride (elements).
+template <typename T>
+struct Batched {
+  T* ptr;
+  long long stride;
+  int ld;
+};
+
+}  // namespace nne
+
+#define NNE_CUDA_TRY(expr)                                                   \
+  do {                                                                       \
+    cudaError_t _e = (expr);                                                 \
+    if (_e != cudaSuccess) return nne::set_cuda_error(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+namespace nne {
+nne_status set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+nne_status set_error(nne_status s, const char* fmt, ...);
+}  // namespace nne

@@ -1,0 +1,318 @@
+// Batched complex GEMM (SIMT), the superoperator epilogue, and small
+// elementwise / reduction kernels used by the gate step.
+#include "kernels.cuh"
+
+namespace nne {
+
+// C[z] = alpha * op(A[z]) * op(B[z]) + beta * C[z], row-major, M x N x K.
+// op N: element (i, k) of A is A[i * lda + k]; op C: conj(A[k * lda + i]).
+template <typename R, int OPA, int OPB>
+__global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K, cx<R> alpha,
+                                                     const cx<R>* __restrict__ A, long long sA, int lda,
+                                                     const cx<R>* __restrict__ B, long long sB, int ldb,
+                                                     cx<R> beta, cx<R>* __restrict__ C, long long sC, int ldc) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ cx<R> As[BK][BM];
+  __shared__ cx<R> Bs[BK][BN];
+  const int z = blockIdx.z;
+  A += z * sA;
+  B += z * sB;
+  C += z * sC;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = tid; e < BM * BK; e += 256) {
+      int i, k;
+      if (OPA == OP_N) { k = e % BK; i = e / BK; } else { i = e % BM; k = e / BM; }
+      const int gi = row0 + i, gk = k0 + k;
+      cx<R> v = mk<R>(0, 0);
+      if (gi < M && gk < K) v = (OPA == OP_N) ? A[(long long)gi * lda + gk] : conj(A[(long long)gk * lda + gi]);
+      As[k][i] = v;
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      int j, k;
+      if (OPB == OP_N) { j = e % BN; k = e / BN; } else { k = e % BK; j = e / BK; }
+      const int gj = col0 + j, gk = k0 + k;
+      cx<R> v = mk<R>(0, 0);
+      if (gj < N && gk < K) v = (OPB == OP_N) ? B[(long long)gk * ldb + gj] : conj(B[(long long)gj * ldb + gk]);
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      cx<R> a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) fma_(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  const bool use_beta = (beta.re != R(0) || beta.im != R(0));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = row0 + ty + 16 * i;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = col0 + tx + 16 * j;
+      if (gj >= N) continue;
+      cx<R> v = alpha * acc[i][j];
+      cx<R>* c = C + (long long)gi * ldc + gj;
+      if (use_beta) v = v + beta * (*c);
+      *c = v;
+    }
+  }
+}
+
+template <typename R>
+cudaError_t cgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<R> alpha, const cx<R>* A,
+                  long long sA, int lda, const cx<R>* B, long long sB, int ldb, cx<R> beta, cx<R>* C,
+                  long long sC, int ldc, int batch) {
+  if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  if (opA == OP_N && opB == OP_N)
+    cgemm_kernel<R, OP_N, OP_N><<<grid, 256, 0, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC, ldc);
+  else if (opA == OP_N && opB == OP_C)
+    cgemm_kernel<R, OP_N, OP_C><<<grid, 256, 0, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC, ldc);
+  else if (opA == OP_C && opB == OP_N)
+    cgemm_kernel<R, OP_C, OP_N><<<grid, 256, 0, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC, ldc);
+  else
+    cgemm_kernel<R, OP_C, OP_C><<<grid, 256, 0, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC, ldc);
+  return cudaGetLastError();
+}
+
+// In-place superoperator on X = theta ((4 dl) x (4 dr), rows (a, s1), cols (s2, b)):
+// X[a,s1',s2',b] = sum_{s1,s2} G[4 s1' + s2'][4 s1 + s2] X[a,s1,s2,b].
+// One thread per (a, b) holds all 16 (s1, s2) entries.
+template <typename R>
+__global__ void __launch_bounds__(256) apply_superop_kernel(cx<R>* X, long long sX, int dl, int dr,
+                                                             const double* __restrict__ G, long long sG) {
+  __shared__ cx<R> g[256];
+  const int z = blockIdx.z;
+  X += z * sX;
+  G += 2 * z * sG;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) g[i] = mk<R>((R)G[2 * i], (R)G[2 * i + 1]);
+  __syncthreads();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)dl * dr) return;
+  const int a = (int)(idx / dr), b = (int)(idx % dr);
+  const long long ld = 4LL * dr;
+  cx<R> t[16];
+#pragma unroll
+  for (int s1 = 0; s1 < 4; ++s1)
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) t[4 * s1 + s2] = X[(4LL * a + s1) * ld + (long long)s2 * dr + b];
+#pragma unroll
+  for (int u1 = 0; u1 < 4; ++u1)
+#pragma unroll
+    for (int u2 = 0; u2 < 4; ++u2) {
+      cx<R> acc = mk<R>(0, 0);
+#pragma unroll
+      for (int v = 0; v < 16; ++v) fma_(acc, g[16 * (4 * u1 + u2) + v], t[v]);
+      X[(4LL * a + u1) * ld + (long long)u2 * dr + b] = acc;
+    }
+}
+
+template <typename R>
+cudaError_t apply_superop(cudaStream_t st, cx<R>* X, long long sX, int dl, int dr, const double* G, long long sG,
+                          int batch) {
+  const long long work = (long long)dl * dr;
+  dim3 grid((unsigned)((work + 255) / 256), 1, batch);
+  apply_superop_kernel<R><<<grid, 256, 0, st>>>(X, sX, dl, dr, G, sG);
+  return cudaGetLastError();
+}
+
+// Partial sums of |x|^2 over `count` elements per batch entry, `parts` blocks per
+// entry; partial p of entry z goes to out[z * parts + p] (deterministic order).
+template <typename R>
+__global__ void __launch_bounds__(256) sumsq_partial_kernel(const cx<R>* X, long long sX, long long count,
+                                                             double* out, int parts) {
+  const int z = blockIdx.y;
+  X += z * sX;
+  double s = 0;
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < count; i += (long long)parts * 256) {
+    cx<R> v = X[i];
+    s += (double)v.re * v.re + (double)v.im * v.im;
+  }
+  s = warp_sum_r(s);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[z * parts + blockIdx.x] = t;
+  }
+}
+
+template <typename R>
+cudaError_t sumsq_partial(cudaStream_t st, const cx<R>* X, long long sX, long long count, double* out, int parts,
+                          int batch) {
+  dim3 grid(parts, batch);
+  sumsq_partial_kernel<R><<<grid, 256, 0, st>>>(X, sX, count, out, parts);
+  return cudaGetLastError();
+}
+
+// Gate bookkeeping per instance: kept = sum of kept parts, total = sum of total
+// parts; scale[z] = 1/sqrt(kept); log_norm += log sqrt(kept); log_fid += log(kept/total).
+__global__ void finish_gate_kernel(const double* kept_parts, const double* total_parts, int parts, int batch,
+                                   double* scale, double* log_norm, double* log_fid, int* err) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= batch) return;
+  double kept = 0, total = 0;
+  for (int p = 0; p < parts; ++p) kept += kept_parts[z * parts + p];
+  if (total_parts) {
+    for (int p = 0; p < parts; ++p) total += total_parts[z * parts + p];
+  } else {
+    total = kept;
+  }
+  if (!(kept > 0) || !(total > 0) || !isfinite(kept) || !isfinite(total)) {
+    atomicExch(err, NNE_ERR_NOCONV);
+    scale[z] = 1.0;
+    return;
+  }
+  const double nrm = sqrt(kept);
+  scale[z] = 1.0 / nrm;
+  log_norm[z] += log(nrm);
+  double f = kept / total;
+  if (f > 1.0) f = 1.0;
+  log_fid[z] += log(f);
+}
+
+template <typename R>
+__global__ void scale_kernel(cx<R>* X, long long sX, long long count, const double* scale) {
+  const int z = blockIdx.y;
+  const R s = (R)scale[z];
+  X += z * sX;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    X[i] = s * X[i];
+}
+
+template <typename R>
+cudaError_t scale_batched(cudaStream_t st, cx<R>* X, long long sX, long long count, const double* scale, int batch) {
+  int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  scale_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, count, scale);
+  return cudaGetLastError();
+}
+
+// Y[z] (cols x rows) = conj(X[z])^T or X[z]^T (rows x cols), row-major both.
+template <typename R, bool CONJ>
+__global__ void transpose_kernel(const cx<R>* X, long long sX, int rows, int cols, int ldx, cx<R>* Y, long long sY,
+                                 int ldy) {
+  __shared__ cx<R> tile[32][33];
+  const int z = blockIdx.z;
+  X += z * sX;
+  Y += z * sY;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = X[(long long)r * ldx + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) {
+      cx<R> v = tile[threadIdx.x][i];
+      Y[(long long)c * ldy + r] = CONJ ? conj(v) : v;
+    }
+  }
+}
+
+template <typename R>
+cudaError_t transpose(cudaStream_t st, bool conj_, const cx<R>* X, long long sX, int rows, int cols, int ldx,
+                      cx<R>* Y, long long sY, int ldy, int batch) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
+  dim3 block(32, 8);
+  if (conj_)
+    transpose_kernel<R, true><<<grid, block, 0, st>>>(X, sX, rows, cols, ldx, Y, sY, ldy);
+  else
+    transpose_kernel<R, false><<<grid, block, 0, st>>>(X, sX, rows, cols, ldx, Y, sY, ldy);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void conj_inplace_kernel(cx<R>* X, long long sX, long long count) {
+  X += blockIdx.y * sX;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    X[i].im = -X[i].im;
+}
+
+template <typename R>
+cudaError_t conj_inplace(cudaStream_t st, cx<R>* X, long long sX, long long count, int batch) {
+  int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  conj_inplace_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, count);
+  return cudaGetLastError();
+}
+
+// Rows x cols identity (1 on the diagonal of the leading square block).
+template <typename R>
+__global__ void identity_kernel(cx<R>* X, long long sX, int rows, int cols) {
+  X += blockIdx.y * sX;
+  const long long count = (long long)rows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / cols), c = (int)(i % cols);
+    X[i] = mk<R>(r == c ? R(1) : R(0), R(0));
+  }
+}
+
+template <typename R>
+cudaError_t identity(cudaStream_t st, cx<R>* X, long long sX, int rows, int cols, int batch) {
+  const long long count = (long long)rows * cols;
+  int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  identity_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, rows, cols);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void copy_kernel(const cx<R>* X, long long sX, cx<R>* Y, long long sY, long long count) {
+  X += blockIdx.y * sX;
+  Y += blockIdx.y * sY;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    Y[i] = X[i];
+}
+
+template <typename R>
+cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y, long long sY, long long count,
+                         int batch) {
+  int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  copy_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, Y, sY, count);
+  return cudaGetLastError();
+}
+
+#define NNE_INST_BLAS(R)                                                                                         \
+  template cudaError_t cgemm<R>(cudaStream_t, int, int, int, int, int, cx<R>, const cx<R>*, long long, int,     \
+                                const cx<R>*, long long, int, cx<R>, cx<R>*, long long, int, int);              \
+  template cudaError_t apply_superop<R>(cudaStream_t, cx<R>*, long long, int, int, const double*, long long, int); \
+  template cudaError_t sumsq_partial<R>(cudaStream_t, const cx<R>*, long long, long long, double*, int, int);     \
+  template cudaError_t scale_batched<R>(cudaStream_t, cx<R>*, long long, long long, const double*, int);          \
+  template cudaError_t transpose<R>(cudaStream_t, bool, const cx<R>*, long long, int, int, int, cx<R>*, long long, \
+                                    int, int);                                                                   \
+  template cudaError_t conj_inplace<R>(cudaStream_t, cx<R>*, long long, long long, int);                         \
+  template cudaError_t identity<R>(cudaStream_t, cx<R>*, long long, int, int, int);                              \
+  template cudaError_t copy_batched<R>(cudaStream_t, const cx<R>*, long long, cx<R>*, long long, long long, int);
+
+NNE_INST_BLAS(float)
+NNE_INST_BLAS(double)
+
+cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, int parts, int batch,
+                        double* scale, double* log_norm, double* log_fid, int* err) {
+  finish_gate_kernel<<<(batch + 127) / 128, 128, 0, st>>>(kept_parts, total_parts, parts, batch, scale, log_norm,
+                                                          log_fid, err);
+  return cudaGetLastError();
+}
+
+}  // namespace nne

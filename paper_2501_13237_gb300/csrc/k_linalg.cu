@@ -1,0 +1,580 @@
+// Dense linear algebra of the truncation step, written for GB300:
+//   * Householder reduction of a Hermitian matrix to real tridiagonal form,
+//     one thread-block cluster per matrix (hardware cluster barriers, matrix
+//     resident in L2), two cluster barriers per column;
+//   * eigenvalues of the tridiagonal by 32-way multisection with Sturm
+//     counts (one warp per wanted eigenvalue);
+//   * eigenvectors by inverse iteration with a partially pivoted tridiagonal
+//     LU (one thread per eigenvector), back-transformed through the phase
+//     scaling and the Householder reflectors (one CTA per 32 columns);
+//   * Householder QR (one cluster per matrix, column blocks owned by CTAs,
+//     one cluster barrier per column) and explicit Q formation; used to
+//     orthonormalise the eigenvector block and for the centre moves.
+// Precision follows the state: float for complex64 states, double for
+// complex128.  The reductions are written in a fixed order, so results are
+// bitwise reproducible run to run and independent of what else is batched.
+#include "kernels.cuh"
+#include <float.h>
+
+namespace cg = cooperative_groups;
+
+namespace nne {
+
+template <typename R> struct Lim;
+template <> struct Lim<float> {
+  static __device__ __forceinline__ float eps() { return FLT_EPSILON; }
+  static __device__ __forceinline__ float tiny() { return FLT_MIN; }
+  static __device__ __forceinline__ float big() { return 1e30f; }
+};
+template <> struct Lim<double> {
+  static __device__ __forceinline__ double eps() { return DBL_EPSILON; }
+  static __device__ __forceinline__ double tiny() { return DBL_MIN; }
+  static __device__ __forceinline__ double big() { return 1e250; }
+};
+
+// Sum over the block in a fixed order; every thread gets the total.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  v = warp_sum_r(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T t = 0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+// Householder vector of x (length m, in smem v, overwritten): P = I - 2 v v^H,
+// P x = alpha e_1.  Returns alpha.  Whole block participates.
+template <typename R>
+__device__ cx<R> householder(cx<R>* v, int m, double* red) {
+  double s = 0;
+  for (int t = threadIdx.x; t < m; t += blockDim.x) s += (double)norm2(v[t]);
+  const double xn2 = block_sum(s, red);
+  const cx<R> x0 = v[0];
+  const double ax0 = sqrt((double)norm2(x0));
+  const double xn = sqrt(xn2);
+  cx<R> alpha = mk<R>(0, 0);
+  double un = 0;
+  if (xn > 0) {
+    const double pr = ax0 > 0 ? (double)x0.re / ax0 : 1.0, pi = ax0 > 0 ? (double)x0.im / ax0 : 0.0;
+    alpha = mk<R>((R)(-xn * pr), (R)(-xn * pi));
+    un = sqrt(2.0 * xn2 + 2.0 * xn * ax0);
+  }
+  __syncthreads();
+  const R inv = un > 0 ? (R)(1.0 / un) : R(0);
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    cx<R> u = v[t];
+    if (t == 0) u = u - alpha;
+    v[t] = inv * u;
+  }
+  __syncthreads();
+  return alpha;
+}
+
+// ---------------------------------------------------------------- tridiagonal
+// H (n x n) -> real tridiagonal d, complex subdiagonal e (e[k] = T[k+1][k]);
+// reflector j (length n-j-1) is stored in row j of H, columns j+1..n-1.
+template <typename R>
+__global__ void __launch_bounds__(256) tridiag_kernel(cx<R>* Hb, long long sH, int n, R* db, cx<R>* eb, int ldde,
+                                                       cx<R>* Pb, double* Kb) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int z = blockIdx.y;
+  cx<R>* H = Hb + z * sH;
+  R* d = db + (long long)z * ldde;
+  cx<R>* e = eb + (long long)z * ldde;
+  cx<R>* P = Pb + (long long)z * ldde;
+  double* Kp = Kb + z * 32;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* v = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* w = v + n;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  const int gw = rank * nw + warp, GW = CS * nw;
+
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    const cx<R>* rowj = H + (long long)j * n + (j + 1);
+    for (int t = tid; t < m; t += nth) v[t] = conj(rowj[t]);   // column j below the diagonal
+    __syncthreads();
+    const R djj = H[(long long)j * n + j].re;
+    const cx<R> alpha = householder(v, m, red);
+    if (rank == 0 && tid == 0) {
+      d[j] = djj;
+      e[j] = alpha;
+    }
+    // p = A v on own rows; partial of K = v^H p
+    double kp = 0;
+    for (int t = gw; t < m; t += GW) {
+      const cx<R>* row = H + (long long)(j + 1 + t) * n + (j + 1);
+      cx<R> acc = mk<R>(0, 0);
+      for (int k = lane; k < m; k += 32) fma_(acc, row[k], v[k]);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        P[t] = acc;
+        kp += (double)v[t].re * acc.re + (double)v[t].im * acc.im;
+      }
+    }
+    kp = block_sum(kp, red);
+    if (tid == 0) Kp[rank] = kp;
+    __threadfence();
+    cluster.sync();
+    double K = 0;
+    for (int c = 0; c < CS; ++c) K += Kp[c];
+    const R twoK = (R)(2.0 * K);
+    for (int t = tid; t < m; t += nth) {
+      const cx<R> p = P[t];
+      w[t] = mk<R>(2 * p.re - twoK * v[t].re, 2 * p.im - twoK * v[t].im);
+    }
+    if (rank == 0) {
+      cx<R>* rj = H + (long long)j * n + (j + 1);
+      for (int t = tid; t < m; t += nth) rj[t] = v[t];      // keep reflector j for the back-transform
+    }
+    __syncthreads();
+    for (int t = gw; t < m; t += GW) {
+      cx<R>* row = H + (long long)(j + 1 + t) * n + (j + 1);
+      const cx<R> vt = v[t], wt = w[t];
+      for (int k = lane; k < m; k += 32) {
+        cx<R> a = row[k];
+        const cx<R> wk = w[k], vk = v[k];
+        // a -= vt conj(wk) + wt conj(vk)
+        a.re -= vt.re * wk.re + vt.im * wk.im + wt.re * vk.re + wt.im * vk.im;
+        a.im -= vt.im * wk.re - vt.re * wk.im + wt.im * vk.re - wt.re * vk.im;
+        row[k] = a;
+      }
+    }
+    __threadfence();
+    cluster.sync();
+  }
+  if (rank == 0 && tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = H[(long long)(n - 2) * n + (n - 2)].re;
+      d[n - 1] = H[(long long)(n - 1) * n + (n - 1)].re;
+      e[n - 2] = H[(long long)(n - 1) * n + (n - 2)];
+    } else {
+      d[0] = H[0].re;
+    }
+  }
+}
+
+// |e_k| and the phases phi (phi_0 = 1, phi_{k+1} = phi_k e_k/|e_k|) that make
+// the tridiagonal real: T = D T' D^H with T'_{k+1,k} = |e_k|.
+template <typename R>
+__global__ void tridiag_phases_kernel(const cx<R>* eb, int n, int ldde, R* eabs, cx<R>* phib, int batch) {
+  const int z = blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= batch) return;
+  const cx<R>* e = eb + (long long)z * ldde;
+  R* ea = eabs + (long long)z * ldde;
+  cx<R>* phi = phib + (long long)z * ldde;
+  cx<double> p = mk<double>(1.0, 0.0);
+  phi[0] = mk<R>(1, 0);
+  for (int k = 0; k + 1 < n; ++k) {
+    const double er = e[k].re, ei = e[k].im;
+    const double a = sqrt(er * er + ei * ei);
+    ea[k] = (R)a;
+    if (a > 0) p = p * mk<double>(er / a, ei / a);
+    const double pa = sqrt(p.re * p.re + p.im * p.im);
+    p = mk<double>(p.re / pa, p.im / pa);
+    phi[k + 1] = mk<R>((R)p.re, (R)p.im);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ int sturm_count(const R* d, const R* e, int n, R x, R pivmin) {
+  R q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  int c = q < R(0);
+  for (int k = 1; k < n; ++k) {
+    q = (d[k] - x) - (e[k - 1] * e[k - 1]) / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    c += q < R(0);
+  }
+  return c;
+}
+
+// Top r eigenvalues (descending) of the real tridiagonal (d, e): one warp each.
+template <typename R>
+__global__ void bisect_kernel(const R* db, const R* eb, int n, int r, int ldde, R* lamb, int ldl, int total) {
+  const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gw >= total) return;
+  const int z = gw / r, t = gw % r;
+  const R* d = db + (long long)z * ldde;
+  const R* e = eb + (long long)z * ldde;
+  R lo = Lim<R>::big(), hi = -Lim<R>::big(), emax = 0;
+  for (int k = lane; k < n; k += 32) {
+    const R rad = (k > 0 ? e[k - 1] : R(0)) + (k + 1 < n ? e[k] : R(0));
+    lo = fmin(lo, d[k] - rad);
+    hi = fmax(hi, d[k] + rad);
+    if (k + 1 < n) emax = fmax(emax, e[k]);
+  }
+  for (int m = 16; m > 0; m >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, m));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, m));
+    emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, m));
+  }
+  const R tnorm = fmax(fabs(lo), fabs(hi));
+  const R pivmin = Lim<R>::tiny() * fmax(R(1), emax * emax);
+  const R eps = Lim<R>::eps();
+  lo -= 4 * eps * tnorm + pivmin;
+  hi += 4 * eps * tnorm + pivmin;
+  const int idx = n - 1 - t;     // ascending index of the wanted eigenvalue
+  const R tol = 2 * eps * tnorm + 2 * pivmin;
+  for (int it = 0; it < 64 && (hi - lo) > tol; ++it) {
+    const R x = lo + (hi - lo) * (R)(lane + 1) / R(33);
+    const int cnt = sturm_count(d, e, n, x, pivmin);
+    const unsigned mask = __ballot_sync(0xffffffffu, cnt <= idx);
+    R nlo = lo, nhi = hi;
+    if (mask) {
+      const int l = 31 - __clz(mask);
+      nlo = __shfl_sync(0xffffffffu, x, l);
+      const R xn = __shfl_sync(0xffffffffu, x, (l + 1) & 31);
+      if (l < 31) nhi = xn;
+    } else {
+      nhi = __shfl_sync(0xffffffffu, x, 0);
+    }
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) lamb[(long long)z * ldl + t] = R(0.5) * (lo + hi);
+}
+
+__device__ __forceinline__ unsigned long long splitmix(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+// Inverse iteration for eigenvalue lam[t] of the real tridiagonal (d, e):
+// 3 solves with the partially pivoted LU of (T - lam I); tiny pivots are
+// replaced by eps*||T||.  Output column t of Z (n x r, row-major).
+template <typename R>
+__global__ void inviter_kernel(const R* db, const R* eb, int n, int r, int ldde, const R* lamb, int ldl, R* Zb,
+                               long long sZ, R* Lb, R* U0b, R* U1b, R* U2b, uint8_t* pivb, long long sS, int total) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int z = gid / r, t = gid % r;
+  const R* d = db + (long long)z * ldde;
+  const R* e = eb + (long long)z * ldde;
+  const R lam = lamb[(long long)z * ldl + t];
+  R* y = Zb + z * sZ;
+  R* L = Lb + z * sS;
+  R* U0 = U0b + z * sS;
+  R* U1 = U1b + z * sS;
+  R* U2 = U2b + z * sS;
+  uint8_t* piv = pivb + z * sS;
+  R tnorm = 0;
+  for (int k = 0; k < n; ++k) {
+    const R rad = (k > 0 ? e[k - 1] : R(0)) + (k + 1 < n ? e[k] : R(0));
+    tnorm = fmax(tnorm, fabs(d[k]) + rad);
+  }
+  if (tnorm == R(0)) tnorm = R(1);
+  const R tiny = Lim<R>::eps() * tnorm;
+  // factor
+  R diag = d[0] - lam, sup1 = n > 1 ? e[0] : R(0);
+  for (int k = 0; k + 1 < n; ++k) {
+    const R sub = e[k], nd = d[k + 1] - lam, ns = (k + 2 < n) ? e[k + 1] : R(0);
+    const long long o = (long long)k * r + t;
+    if (fabs(diag) >= fabs(sub)) {
+      const R l = diag != R(0) ? sub / diag : R(0);
+      piv[o] = 0; L[o] = l; U0[o] = diag; U1[o] = sup1; U2[o] = 0;
+      diag = nd - l * sup1;
+      sup1 = ns;
+    } else {
+      const R l = diag / sub;
+      piv[o] = 1; L[o] = l; U0[o] = sub; U1[o] = nd; U2[o] = ns;
+      diag = sup1 - l * nd;
+      sup1 = -l * ns;
+    }
+  }
+  U0[(long long)(n - 1) * r + t] = diag;
+  // start vector
+  for (int k = 0; k < n; ++k) {
+    const unsigned long long h = splitmix(((unsigned long long)z << 40) ^ ((unsigned long long)t << 20) ^ (unsigned long long)k);
+    y[(long long)k * r + t] = (R)((double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+  }
+  const R big = Lim<R>::big();
+  for (int it = 0; it < 3; ++it) {
+    for (int k = 0; k + 1 < n; ++k) {
+      const long long o = (long long)k * r + t, o1 = o + r;
+      R yk = y[o], yk1 = y[o1];
+      if (piv[o]) { const R tmp = yk; yk = yk1; yk1 = tmp; y[o] = yk; }
+      y[o1] = yk1 - L[o] * yk;
+    }
+    for (int k = n - 1; k >= 0; --k) {
+      const long long o = (long long)k * r + t;
+      R u0 = U0[o];
+      if (fabs(u0) < tiny) u0 = u0 < R(0) ? -tiny : tiny;
+      R acc = y[o];
+      if (k + 1 < n) acc -= U1[o] * y[o + r];
+      if (k + 2 < n) acc -= U2[o] * y[o + 2 * r];
+      R yk = acc / u0;
+      if (!(fabs(yk) < big)) {
+        // rescale everything computed so far and the untouched right-hand side
+        const R s = isfinite(yk) ? R(1) / fabs(yk) : R(0);
+        for (int i = 0; i < n; ++i) y[(long long)i * r + t] *= s;
+        yk = isfinite(yk) ? yk * s : R(1);
+      }
+      y[o] = yk;
+    }
+    R mx = 0;
+    for (int k = 0; k < n; ++k) mx = fmax(mx, fabs(y[(long long)k * r + t]));
+    if (!(mx > R(0))) mx = R(1);
+    double s2 = 0;
+    for (int k = 0; k < n; ++k) {
+      const R v = y[(long long)k * r + t] / mx;
+      s2 += (double)v * v;
+    }
+    const R inv = (R)(1.0 / (sqrt(s2) * (double)mx));
+    for (int k = 0; k < n; ++k) y[(long long)k * r + t] *= inv;
+  }
+}
+
+// U[row0 + i][c] -= 2 v_i (v^H U[row0.., c]) for one 32-column block; warp w
+// owns rows congruent to w mod 8 (absolute), so only `red` is shared.
+template <typename R>
+__device__ __forceinline__ void reflect_colblock(cx<R>* U, int ldu, int c, bool active, const cx<R>* v, int row0,
+                                                 int len, cx<R> (*red)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int first = row0 + ((warp - row0 % 8) + 8) % 8;
+  cx<R> p = mk<R>(0, 0);
+  if (active)
+    for (int row = first; row < row0 + len; row += 8) fmac_(p, v[row - row0], U[(long long)row * ldu + c]);
+  red[warp][lane] = p;
+  __syncthreads();
+  cx<R> s = mk<R>(0, 0);
+  for (int w = 0; w < 8; ++w) s = s + red[w][lane];
+  __syncthreads();
+  if (active) {
+    const cx<R> s2 = mk<R>(2 * s.re, 2 * s.im);
+    for (int row = first; row < row0 + len; row += 8) {
+      const cx<R> vi = v[row - row0];
+      cx<R>& u = U[(long long)row * ldu + c];
+      u = u - vi * s2;
+    }
+  }
+}
+
+// U = Q_house D Z for a 32-column block: start from phi_k Z[k][c], apply
+// reflectors n-3 .. 0 (reflector j in row j of H, acting on rows j+1..).
+template <typename R>
+__global__ void __launch_bounds__(256) backtransform_kernel(const cx<R>* Hb, long long sH, int n, int r,
+                                                             const cx<R>* phib, int ldde, const R* Zb, long long sZ,
+                                                             cx<R>* Ub, long long sU) {
+  __shared__ cx<R> red[8][32];
+  const int z = blockIdx.y;
+  const cx<R>* H = Hb + z * sH;
+  const cx<R>* phi = phib + (long long)z * ldde;
+  const R* Z = Zb + z * sZ;
+  cx<R>* U = Ub + z * sU;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const bool active = c < r;
+  if (active)
+    for (int k = warp; k < n; k += 8) U[(long long)k * r + c] = Z[(long long)k * r + c] * phi[k];
+  for (int j = n - 3; j >= 0; --j) {
+    reflect_colblock(U, r, c, active, H + (long long)j * n + (j + 1), j + 1, n - j - 1, red);
+  }
+}
+
+// ---------------------------------------------------------------- QR
+// Factor A (m x n, row-major) in place: reflector j (length m-j) to V row j;
+// column blocks of 32 owned by CTA (block % CS).  A[j][j] = alpha_j, and
+// A[i][j] = 0 for i > j, so the upper triangle of A is R on exit.
+template <typename R>
+__global__ void __launch_bounds__(256) qr_factor_kernel(cx<R>* Ab, long long sA, int m, int n, cx<R>* Vb,
+                                                         long long sV) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int z = blockIdx.y;
+  cx<R>* A = Ab + z * sA;
+  cx<R>* V = Vb + z * sV;
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* v = reinterpret_cast<cx<R>*>(smem_raw);
+  __shared__ cx<R> red[8][32];
+  __shared__ double dred[32];
+  const int lane = threadIdx.x & 31;
+  const int nblk = (n + 31) / 32;
+  const int k = min(m, n);
+  for (int j = 0; j < k; ++j) {
+    const int mj = m - j;
+    const int owner = (j / 32) % CS;
+    if (rank == owner) {
+      for (int t = threadIdx.x; t < mj; t += blockDim.x) v[t] = A[(long long)(j + t) * n + j];
+      __syncthreads();
+      const cx<R> alpha = householder(v, mj, dred);
+      for (int t = threadIdx.x; t < mj; t += blockDim.x) {
+        V[(long long)j * m + t] = v[t];
+        A[(long long)(j + t) * n + j] = t == 0 ? alpha : mk<R>(0, 0);
+      }
+      __threadfence();
+    }
+    cluster.sync();
+    if (rank != owner) {
+      for (int t = threadIdx.x; t < mj; t += blockDim.x) v[t] = V[(long long)j * m + t];
+    }
+    __syncthreads();
+    for (int b = rank; b < nblk; b += CS) {
+      if (32 * b + 31 <= j) continue;
+      const int c = 32 * b + lane;
+      reflect_colblock(A, n, c, c > j && c < n, v, j, mj, red);
+      __syncthreads();
+    }
+  }
+}
+
+// Q (m x k, ld = k) = P_0 ... P_{k-1} [I_k; 0] for one 32-column block.
+template <typename R>
+__global__ void __launch_bounds__(256) qr_formq_kernel(const cx<R>* Vb, long long sV, int m, int k, cx<R>* Qb,
+                                                        long long sQ) {
+  __shared__ cx<R> red[8][32];
+  const int z = blockIdx.y;
+  const cx<R>* V = Vb + z * sV;
+  cx<R>* Q = Qb + z * sQ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const bool inb = c < k;
+  if (inb)
+    for (int i = warp; i < m; i += 8) Q[(long long)i * k + c] = mk<R>(i == c ? R(1) : R(0), R(0));
+  const int jmax = min(k - 1, blockIdx.x * 32 + 31);
+  for (int j = jmax; j >= 0; --j) {
+    reflect_colblock(Q, k, c, inb && c >= j, V + (long long)j * m, j, m - j, red);
+  }
+}
+
+template <typename R>
+__global__ void qr_extract_r_kernel(const cx<R>* Ab, long long sA, int m, int n, cx<R>* Rb, long long sR) {
+  const int z = blockIdx.y;
+  const cx<R>* A = Ab + z * sA;
+  cx<R>* Rm = Rb + z * sR;
+  const int k = min(m, n);
+  const long long count = (long long)k * n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const int row = (int)(i / n), col = (int)(i % n);
+    Rm[i] = col >= row ? A[(long long)row * n + col] : mk<R>(0, 0);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename K, typename... Args>
+static cudaError_t launch_cluster(K kernel, int cs, int batch, size_t smem, cudaStream_t st, Args... args) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (cs > 8) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, batch, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+static int cluster_size_for(int n) { return n >= 512 ? 8 : (n >= 128 ? 4 : (n >= 32 ? 2 : 1)); }
+
+EighWork eigh_workspace(int n, int r) {
+  EighWork w;
+  const long long qn = std::max(n, r);
+  // cx: e (n), phi (n), P (n), QR reflectors (r x n)
+  w.cx_elems = 3LL * n + (long long)r * n + 32;
+  // re: d, eabs (n each), lam (r), Z (n r), L/U0/U1/U2 (4 n r), Kpart (32 doubles = 64 floats)
+  w.re_elems = 2LL * n + r + 5LL * n * r + 64 + qn;
+  w.u8_elems = (long long)n * r;
+  return w;
+}
+
+QrWork qr_workspace(int m, int n) {
+  QrWork w;
+  w.cx_elems = (long long)std::min(m, n) * m;
+  return w;
+}
+
+template <typename R>
+cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, long long sQ, cx<R>* Rout,
+               long long sR, void* cx_ws, int batch) {
+  const int k = std::min(m, n);
+  if (k <= 0 || batch <= 0) return cudaSuccess;
+  cx<R>* V = reinterpret_cast<cx<R>*>(cx_ws);
+  const long long sV = (long long)k * m;
+  const int cs = std::min(cluster_size_for(std::max(m, n)), (n + 31) / 32);
+  cudaError_t e = launch_cluster(qr_factor_kernel<R>, std::max(cs, 1), batch, sizeof(cx<R>) * (size_t)m, st, A, sA,
+                                 m, n, V, sV);
+  if (e != cudaSuccess) return e;
+  if (Rout) {
+    qr_extract_r_kernel<R><<<dim3(64, batch), 256, 0, st>>>(A, sA, m, n, Rout, sR);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  qr_formq_kernel<R><<<dim3((k + 31) / 32, batch), 256, 0, st>>>(V, sV, m, k, Q, sQ);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R>* U, long long sU, void* cx_ws,
+                     void* re_ws, void* u8_ws, int batch, int* err) {
+  (void)err;
+  if (batch <= 0) return cudaSuccess;
+  const EighWork w = eigh_workspace(n, r);
+  cx<R>* cxb = reinterpret_cast<cx<R>*>(cx_ws);
+  R* reb = reinterpret_cast<R*>(re_ws);
+  uint8_t* u8b = reinterpret_cast<uint8_t*>(u8_ws);
+  // per-batch-entry layouts are interleaved by "ld" strides below
+  const int ldde = n;
+  cx<R>* e = cxb;                                   // batch x n
+  cx<R>* phi = e + (long long)batch * n;            // batch x n
+  cx<R>* P = phi + (long long)batch * n;            // batch x n
+  cx<R>* qrws = P + (long long)batch * n;           // batch x (r n)
+  R* d = reb;                                       // batch x n
+  R* eabs = d + (long long)batch * n;               // batch x n
+  R* lam = eabs + (long long)batch * n;             // batch x r
+  R* Z = lam + (long long)batch * r;                // batch x n r
+  R* Ls = Z + (long long)batch * n * r;             // 4 arrays of batch x n r
+  R* U0 = Ls + (long long)batch * n * r;
+  R* U1 = U0 + (long long)batch * n * r;
+  R* U2 = U1 + (long long)batch * n * r;
+  double* Kp = reinterpret_cast<double*>(U2 + (long long)batch * n * r + 1);
+  Kp = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Kp) + 15) & ~uintptr_t(15));
+  (void)w;
+  const int cs = cluster_size_for(n);
+  cudaError_t ce = launch_cluster(tridiag_kernel<R>, cs, batch, 2 * sizeof(cx<R>) * (size_t)n, st, H, sH, n, d, e,
+                                  ldde, P, Kp);
+  if (ce != cudaSuccess) return ce;
+  tridiag_phases_kernel<R><<<(batch + 63) / 64, 64, 0, st>>>(e, n, ldde, eabs, phi, batch);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  const int total = batch * r;
+  bisect_kernel<R><<<(total * 32 + 255) / 256, 256, 0, st>>>(d, eabs, n, r, ldde, lam, r, total);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  const long long sS = (long long)n * r;
+  inviter_kernel<R><<<(total + 127) / 128, 128, 0, st>>>(d, eabs, n, r, ldde, lam, r, Z, sS, Ls, U0, U1, U2, u8b,
+                                                         sS, total);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  backtransform_kernel<R><<<dim3((r + 31) / 32, batch), 256, 0, st>>>(H, sH, n, r, phi, ldde, Z, sS, U, sU);
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  // orthonormalise the eigenvector block (QR; Q written over U)
+  return qr<R>(st, U, sU, n, r, U, sU, nullptr, 0, qrws, batch);
+}
+
+#define NNE_INST_LINALG(R)                                                                                       \
+  template cudaError_t qr<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, cx<R>*, long long, \
+                             void*, int);                                                                       \
+  template cudaError_t eigh_top<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, void*, void*, \
+                                   void*, int, int*);
+NNE_INST_LINALG(float)
+NNE_INST_LINALG(double)
+
+}  // namespace nne

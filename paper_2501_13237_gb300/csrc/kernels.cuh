@@ -1,0 +1,81 @@
+// Declarations of the device kernels' host launchers (all enqueue on `st`).
+#pragma once
+#include <algorithm>
+#include "common.cuh"
+
+namespace nne {
+
+// ---- k_blas.cu
+template <typename R>
+cudaError_t cgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<R> alpha, const cx<R>* A, long long sA,
+                  int lda, const cx<R>* B, long long sB, int ldb, cx<R> beta, cx<R>* C, long long sC, int ldc,
+                  int batch);
+template <typename R>
+cudaError_t apply_superop(cudaStream_t st, cx<R>* X, long long sX, int dl, int dr, const double* G, long long sG,
+                          int batch);
+template <typename R>
+cudaError_t sumsq_partial(cudaStream_t st, const cx<R>* X, long long sX, long long count, double* out, int parts,
+                          int batch);
+cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, int parts, int batch,
+                        double* scale, double* log_norm, double* log_fid, int* err);
+template <typename R>
+cudaError_t scale_batched(cudaStream_t st, cx<R>* X, long long sX, long long count, const double* scale, int batch);
+template <typename R>
+cudaError_t transpose(cudaStream_t st, bool conj_, const cx<R>* X, long long sX, int rows, int cols, int ldx,
+                      cx<R>* Y, long long sY, int ldy, int batch);
+template <typename R>
+cudaError_t conj_inplace(cudaStream_t st, cx<R>* X, long long sX, long long count, int batch);
+template <typename R>
+cudaError_t identity(cudaStream_t st, cx<R>* X, long long sX, int rows, int cols, int batch);
+template <typename R>
+cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y, long long sY, long long count,
+                         int batch);
+
+// ---- k_linalg.cu
+// Workspace sizes (elements) for eigh_top on n x n matrices with r wanted vectors.
+struct EighWork {
+  long long cx_elems;    // complex R elements
+  long long re_elems;    // real R elements
+  long long u8_elems;    // bytes
+};
+EighWork eigh_workspace(int n, int r);
+// Top-r eigenvectors of the Hermitian H[z] (n x n, row-major, overwritten),
+// written as U[z] (n x r, row-major, columns ordered by decreasing eigenvalue)
+// with orthonormal columns.  Workspace per batch entry as eigh_workspace.
+template <typename R>
+cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R>* U, long long sU, void* cx_ws,
+                     void* re_ws, void* u8_ws, int batch, int* err);
+
+struct QrWork {
+  long long cx_elems;
+};
+QrWork qr_workspace(int m, int n);
+// Householder QR of A[z] (m x n, row-major, ld = n, overwritten): writes
+// Q[z] (m x k, ld = k, k = min(m, n)) with orthonormal columns and, if Rout
+// is not null, Rout[z] (k x n, ld = n, zero below the diagonal), A = Q R.
+template <typename R>
+cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, long long sQ, cx<R>* Rout,
+               long long sR, void* cx_ws, int batch);
+
+// ---- k_sweep.cu
+// <P> for n_obs Pauli strings on every instance (see nne_expect).
+struct SweepSites {
+  const void* const* site;   // per site k: pointer to instance 0's tensor
+  const long long* stride;   // per site k: elements between instances
+};
+template <typename R>
+cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* const* d_site,
+                         const long long* d_stride, int n_inst, int max_dim, int n_obs, const uint8_t* d_paulis,
+                         const int* d_first, const int* d_last, double* d_env, double* d_envscale,
+                         double* d_out /* n_inst x n_obs x 2 */);
+
+// ---- k_superop.cu
+cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int n_inst, const double* d_rates,
+                           double* d_G, double* d_Snoise /* n_inst x 256 complex128 scratch */);
+
+// ---- k_fit.cu
+cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, const double* d_vals,
+                            const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
+                            const double* d_yzero, double* d_out, int* d_status);
+
+}  // namespace nne

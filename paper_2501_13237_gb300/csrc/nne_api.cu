@@ -1,0 +1,699 @@
+// C ABI of libnne: contexts, states, and the host-side orchestration of the
+// gate step (theta formation, superoperator, truncation, normalisation,
+// centre moves), the expectation sweep and the extrapolation fit.  Every
+// arithmetic step runs in the kernels of k_*.cu; this file only sizes
+// buffers, tracks bond dimensions and enqueues launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace nne {
+
+static thread_local std::string g_last_error;
+
+nne_status set_error(nne_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+nne_status set_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  return set_error(e == cudaErrorMemoryAllocation ? NNE_ERR_OOM : NNE_ERR_CUDA, "%s failed: %s (%s:%d)", what,
+                   cudaGetErrorString(e), file, line);
+}
+
+}  // namespace nne
+
+using namespace nne;
+
+struct nne_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  size_t used = 0;
+};
+
+namespace {
+
+struct DevAlloc {
+  nne_ctx* ctx = nullptr;
+  std::vector<std::pair<void*, size_t>> blocks;
+  nne_status alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->budget && ctx->used + bytes > ctx->budget)
+      return set_error(NNE_ERR_OOM, "HBM budget exceeded: %zu + %zu > %zu bytes", ctx->used, bytes, ctx->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    ctx->used += bytes;
+    blocks.push_back({*p, bytes});
+    return NNE_OK;
+  }
+  void release() {
+    for (auto& b : blocks) {
+      cudaFree(b.first);
+      ctx->used -= b.second;
+    }
+    blocks.clear();
+  }
+};
+
+constexpr int PARTS = 64;   // partial sums per instance for Frobenius norms
+
+}  // namespace
+
+struct nne_state {
+  nne_ctx* ctx = nullptr;
+  int n = 0, chi = 0, n_inst = 0;
+  nne_dtype dtype = NNE_C64;
+  nne_trunc trunc = NNE_TRUNC_EXACT;
+  size_t esz = 8;
+  std::vector<int> dims, cap;
+  int centre = 0;
+  int dmax = 1;
+  std::vector<char*> site;           // instance 0 of site k
+  std::vector<long long> sstride;    // elements between instances of site k
+  DevAlloc mem;
+  double* d_lognorm = nullptr;
+  double* d_logfid = nullptr;
+  double* d_scale = nullptr;
+  double* d_parts = nullptr;   // 2 x n_inst x PARTS
+  int* d_err = nullptr;
+  // workspaces (per instance stride in elements)
+  void* X = nullptr;  long long sX = 0;
+  void* H = nullptr;  long long sH = 0;
+  void* U = nullptr;  long long sU = 0;
+  void* T = nullptr;  long long sT = 0;   // centre-move scratch
+  void* Rm = nullptr; long long sR = 0;
+  void* eig_cx = nullptr;
+  void* eig_re = nullptr;
+  void* eig_u8 = nullptr;
+  void* qr_ws = nullptr;
+  // sweep
+  int* d_dims = nullptr;
+  void** d_site = nullptr;
+  long long* d_stride = nullptr;
+  double* d_env = nullptr;
+  double* d_envscale = nullptr;
+  // randomized truncation
+  void* d_omega = nullptr;
+  int omega_rows = 0, omega_cols = 0, power_iters = 0;
+};
+
+namespace {
+
+template <typename R>
+cx<R>* sp(nne_state* s, int k) { return reinterpret_cast<cx<R>*>(s->site[k]); }
+
+template <typename R>
+nne_status check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return set_cuda_error(e, what, __FILE__, __LINE__);
+  return NNE_OK;
+}
+
+#define TRY(x)                          \
+  do {                                  \
+    nne_status _s = (x);                \
+    if (_s != NNE_OK) return _s;        \
+  } while (0)
+#define CTRY(x) TRY(check<R>((x), #x))
+
+// Norm bookkeeping after a split: kept = ||C||^2, total = ||X||^2 (or kept).
+template <typename R>
+nne_status finish_split(nne_state* s, cx<R>* C, long long sC, long long countC, const cx<R>* Xt, long long sXt,
+                        long long countX) {
+  cudaStream_t st = s->ctx->stream;
+  double* kept = s->d_parts;
+  double* total = s->d_parts + (long long)s->n_inst * PARTS;
+  CTRY(sumsq_partial<R>(st, C, sC, countC, kept, PARTS, s->n_inst));
+  if (Xt) CTRY(sumsq_partial<R>(st, Xt, sXt, countX, total, PARTS, s->n_inst));
+  CTRY(finish_gate(st, kept, Xt ? total : nullptr, PARTS, s->n_inst, s->d_scale, s->d_lognorm, s->d_logfid, s->d_err));
+  CTRY(scale_batched<R>(st, C, sC, countC, s->d_scale, s->n_inst));
+  return NNE_OK;
+}
+
+// Make site c left-isometric by QR and push R into site c+1.
+template <typename R>
+nne_status qr_right(nne_state* s, int c) {
+  cudaStream_t st = s->ctx->stream;
+  const int dl = s->dims[c], dr = s->dims[c + 1], dn = s->dims[c + 2];
+  const int m = 4 * dl, k = std::min(m, dr);
+  cx<R>* M = sp<R>(s, c);
+  cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
+  cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
+  CTRY(qr<R>(st, M, s->sstride[c], m, dr, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));
+  CTRY(copy_batched<R>(st, Q, s->sT, M, s->sstride[c], (long long)m * k, s->n_inst));
+  // next <- R next
+  cx<R>* N = sp<R>(s, c + 1);
+  cx<R>* tmp = reinterpret_cast<cx<R>*>(s->H);
+  CTRY(cgemm<R>(st, OP_N, OP_N, k, 4 * dn, dr, mk<R>(1, 0), Rr, s->sR, dr, N, s->sstride[c + 1], 4 * dn,
+                mk<R>(0, 0), tmp, s->sH, 4 * dn, s->n_inst));
+  CTRY(copy_batched<R>(st, tmp, s->sH, N, s->sstride[c + 1], (long long)k * 4 * dn, s->n_inst));
+  s->dims[c + 1] = k;
+  return NNE_OK;
+}
+
+// Make site c right-isometric by LQ (QR of M^H) and push L into site c-1.
+template <typename R>
+nne_status lq_left(nne_state* s, int c) {
+  cudaStream_t st = s->ctx->stream;
+  const int dp = s->dims[c - 1], dl = s->dims[c], dr = s->dims[c + 1];
+  const int m = 4 * dr, k = std::min(m, dl);
+  cx<R>* M = sp<R>(s, c);
+  cx<R>* Mh = reinterpret_cast<cx<R>*>(s->U);
+  CTRY(transpose<R>(st, true, M, s->sstride[c], dl, m, m, Mh, s->sU, dl, s->n_inst));   // (4dr x dl)
+  cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
+  cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
+  CTRY(qr<R>(st, Mh, s->sU, m, dl, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));          // Q (m x k), R (k x dl)
+  CTRY(transpose<R>(st, true, Q, s->sT, m, k, k, M, s->sstride[c], m, s->n_inst));       // site c = Q^H (k x m)
+  cx<R>* P = sp<R>(s, c - 1);
+  cx<R>* tmp = reinterpret_cast<cx<R>*>(s->H);
+  CTRY(cgemm<R>(st, OP_N, OP_C, 4 * dp, k, dl, mk<R>(1, 0), P, s->sstride[c - 1], dl, Rr, s->sR, dl, mk<R>(0, 0),
+                tmp, s->sH, k, s->n_inst));
+  CTRY(copy_batched<R>(st, tmp, s->sH, P, s->sstride[c - 1], (long long)4 * dp * k, s->n_inst));
+  s->dims[c] = k;
+  return NNE_OK;
+}
+
+template <typename R>
+nne_status move_centre(nne_state* s, int target) {
+  while (s->centre < target) {
+    TRY(qr_right<R>(s, s->centre));
+    s->centre++;
+  }
+  while (s->centre > target) {
+    TRY(lq_left<R>(s, s->centre));
+    s->centre--;
+  }
+  return NNE_OK;
+}
+
+// Top-r left (dir > 0) or right (dir < 0) singular subspace of X[z] as an
+// isometry: exact eigenvectors of the Gram matrix, or the randomized range
+// finder with Rayleigh-Ritz.  Writes W (rows x r, ld r) into s->U.
+template <typename R>
+nne_status subspace(nne_state* s, cx<R>* X, int rows, int cols, int r, int dir) {
+  cudaStream_t st = s->ctx->stream;
+  cx<R>* Hm = reinterpret_cast<cx<R>*>(s->H);
+  cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
+  const int n = dir > 0 ? rows : cols;
+  if (dir > 0)
+    CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, cols, mk<R>(1, 0), X, s->sX, cols, X, s->sX, cols, mk<R>(0, 0), Hm,
+                  s->sH, rows, s->n_inst));
+  else
+    CTRY(cgemm<R>(st, OP_C, OP_N, cols, cols, rows, mk<R>(1, 0), X, s->sX, cols, X, s->sX, cols, mk<R>(0, 0), Hm,
+                  s->sH, cols, s->n_inst));
+  CTRY(eigh_top<R>(st, Hm, s->sH, n, r, W, s->sU, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
+  return NNE_OK;
+}
+
+template <typename R>
+nne_status gate_step(nne_state* s, int q, const double* G, long long sG, int dir) {
+  cudaStream_t st = s->ctx->stream;
+  TRY(move_centre<R>(s, dir > 0 ? q : q + 1));
+  const int dl = s->dims[q], dm = s->dims[q + 1], dr = s->dims[q + 2];
+  const int rows = 4 * dl, cols = 4 * dr;
+  const int r = std::min(s->chi, std::min(rows, cols));
+  cx<R>* A = sp<R>(s, q);
+  cx<R>* B = sp<R>(s, q + 1);
+  cx<R>* X = reinterpret_cast<cx<R>*>(s->X);
+  // a2: theta = A B ; a3: theta' = G theta
+  CTRY(cgemm<R>(st, OP_N, OP_N, rows, cols, dm, mk<R>(1, 0), A, s->sstride[q], dm, B, s->sstride[q + 1], cols,
+                mk<R>(0, 0), X, s->sX, cols, s->n_inst));
+  CTRY(apply_superop<R>(st, X, s->sX, dl, dr, G, sG, s->n_inst));
+  const long long countX = (long long)rows * cols;
+  if (dir > 0) {
+    if (r == rows) {
+      CTRY(identity<R>(st, A, s->sstride[q], rows, r, s->n_inst));
+      CTRY(copy_batched<R>(st, X, s->sX, B, s->sstride[q + 1], countX, s->n_inst));
+      TRY(finish_split<R>(s, B, s->sstride[q + 1], countX, nullptr, 0, 0));
+    } else {
+      TRY(subspace<R>(s, X, rows, cols, r, +1));
+      cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
+      CTRY(copy_batched<R>(st, W, s->sU, A, s->sstride[q], (long long)rows * r, s->n_inst));
+      CTRY(cgemm<R>(st, OP_C, OP_N, r, cols, rows, mk<R>(1, 0), W, s->sU, r, X, s->sX, cols, mk<R>(0, 0), B,
+                    s->sstride[q + 1], cols, s->n_inst));
+      TRY(finish_split<R>(s, B, s->sstride[q + 1], (long long)r * cols, X, s->sX, countX));
+    }
+    s->dims[q + 1] = r;
+    s->centre = q + 1;
+  } else {
+    if (r == cols) {
+      CTRY(identity<R>(st, B, s->sstride[q + 1], r, cols, s->n_inst));
+      CTRY(copy_batched<R>(st, X, s->sX, A, s->sstride[q], countX, s->n_inst));
+      TRY(finish_split<R>(s, A, s->sstride[q], countX, nullptr, 0, 0));
+    } else {
+      TRY(subspace<R>(s, X, rows, cols, r, -1));
+      cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
+      CTRY(transpose<R>(st, true, W, s->sU, cols, r, r, B, s->sstride[q + 1], cols, s->n_inst));
+      CTRY(cgemm<R>(st, OP_N, OP_N, rows, r, cols, mk<R>(1, 0), X, s->sX, cols, W, s->sU, r, mk<R>(0, 0), A,
+                    s->sstride[q], r, s->n_inst));
+      TRY(finish_split<R>(s, A, s->sstride[q], (long long)rows * r, X, s->sX, countX));
+    }
+    s->dims[q + 1] = r;
+    s->centre = q;
+  }
+  return NNE_OK;
+}
+
+template <typename R>
+nne_status compress(nne_state* s, int chi_new) {
+  cudaStream_t st = s->ctx->stream;
+  TRY(move_centre<R>(s, 0));
+  for (int k = 0; k + 1 < s->n; ++k) {
+    const int dl = s->dims[k], dr = s->dims[k + 1], dn = s->dims[k + 2];
+    const int rows = 4 * dl;
+    const int r = std::min(chi_new, std::min(rows, dr));
+    if (r >= dr) {
+      TRY(qr_right<R>(s, k));
+    } else {
+      cx<R>* M = sp<R>(s, k);
+      cx<R>* Hm = reinterpret_cast<cx<R>*>(s->H);
+      cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
+      cx<R>* Cm = reinterpret_cast<cx<R>*>(s->Rm);
+      cx<R>* Xs = reinterpret_cast<cx<R>*>(s->X);
+      CTRY(copy_batched<R>(st, M, s->sstride[k], Xs, s->sX, (long long)rows * dr, s->n_inst));
+      CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, dr, mk<R>(1, 0), Xs, s->sX, dr, Xs, s->sX, dr, mk<R>(0, 0), Hm,
+                    s->sH, rows, s->n_inst));
+      CTRY(eigh_top<R>(st, Hm, s->sH, rows, r, W, s->sU, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
+      CTRY(copy_batched<R>(st, W, s->sU, M, s->sstride[k], (long long)rows * r, s->n_inst));
+      CTRY(cgemm<R>(st, OP_C, OP_N, r, dr, rows, mk<R>(1, 0), W, s->sU, r, Xs, s->sX, dr, mk<R>(0, 0), Cm, s->sR, dr,
+                    s->n_inst));
+      TRY(finish_split<R>(s, Cm, s->sR, (long long)r * dr, Xs, s->sX, (long long)rows * dr));
+      cx<R>* N = sp<R>(s, k + 1);
+      cx<R>* tmp = reinterpret_cast<cx<R>*>(s->T);
+      CTRY(cgemm<R>(st, OP_N, OP_N, r, 4 * dn, dr, mk<R>(1, 0), Cm, s->sR, dr, N, s->sstride[k + 1], 4 * dn,
+                    mk<R>(0, 0), tmp, s->sT, 4 * dn, s->n_inst));
+      CTRY(copy_batched<R>(st, tmp, s->sT, N, s->sstride[k + 1], (long long)r * 4 * dn, s->n_inst));
+      s->dims[k + 1] = r;
+    }
+    s->centre = k + 1;
+  }
+  s->chi = chi_new;
+  return NNE_OK;
+}
+
+nne_status read_err(nne_state* s) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->ctx->stream);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+  e = cudaStreamSynchronize(s->ctx->stream);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  if (h != 0) return set_error(h, "device-side failure status %d (non-finite or zero norm in a gate step)", h);
+  return NNE_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* nne_last_error(void) { return g_last_error.c_str(); }
+
+nne_status nne_ctx_create(int device, void* cuda_stream, size_t hbm_budget_bytes, nne_ctx** out) {
+  if (!out) return set_error(NNE_ERR_ARG, "out is null");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDeviceCount", __FILE__, __LINE__);
+  if (device < 0 || device >= ndev) return set_error(NNE_ERR_ARG, "device %d out of range (%d devices)", device, ndev);
+  nne_ctx* c = new nne_ctx();
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  return NNE_OK;
+}
+
+void nne_ctx_destroy(nne_ctx* ctx) { delete ctx; }
+
+size_t nne_ctx_bytes_in_use(const nne_ctx* ctx) { return ctx ? ctx->used : 0; }
+
+nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_inst, const double* rates,
+                              void* G_out) {
+  if (!ctx || n_gates < 0 || n_inst < 1 || !rates || (n_gates > 0 && (!U || !G_out)))
+    return set_error(NNE_ERR_ARG, "nne_build_superops: bad arguments");
+  for (int i = 0; i < n_inst; ++i)
+    for (int c = 0; c < 4; ++c) {
+      const double p = rates[4 * i + c];
+      const double hi = c == 0 ? 16.0 / 15.0 : 1.0;
+      if (!(p >= 0.0 && p <= hi)) return set_error(NNE_ERR_ARG, "rate %d of instance %d out of range: %g", c, i, p);
+    }
+  DeviceGuard g(ctx->device);
+  double *dU = nullptr, *dR = nullptr, *dS = nullptr;
+  const size_t bu = sizeof(double) * 32 * (size_t)std::max(n_gates, 1), br = sizeof(double) * 4 * n_inst,
+               bs = sizeof(double) * 512 * n_inst;
+  NNE_CUDA_TRY(cudaMalloc(&dU, bu));
+  NNE_CUDA_TRY(cudaMalloc(&dR, br));
+  NNE_CUDA_TRY(cudaMalloc(&dS, bs));
+  nne_status rc = NNE_OK;
+  cudaError_t e = cudaSuccess;
+  if (n_gates > 0) e = cudaMemcpyAsync(dU, U, sizeof(double) * 32 * n_gates, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dR, rates, br, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = build_superops(ctx->stream, n_gates, dU, n_inst, dR, (double*)G_out, dS);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) rc = set_cuda_error(e, "build_superops", __FILE__, __LINE__);
+  cudaFree(dU);
+  cudaFree(dR);
+  cudaFree(dS);
+  return rc;
+}
+
+nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne_dtype dtype, nne_trunc trunc,
+                            const uint8_t* init_bits, nne_state** out) {
+  if (!ctx || !out || n_qubits < 2 || chi < 1 || n_inst < 1 || (dtype != NNE_C64 && dtype != NNE_C128) ||
+      (trunc != NNE_TRUNC_EXACT && trunc != NNE_TRUNC_RSVD))
+    return set_error(NNE_ERR_ARG, "nne_create_state: bad arguments");
+  if (chi > 4096) return set_error(NNE_ERR_ARG, "chi %d above the supported maximum 4096", chi);
+  *out = nullptr;
+  DeviceGuard g(ctx->device);
+  nne_state* s = new nne_state();
+  s->ctx = ctx;
+  s->mem.ctx = ctx;
+  s->n = n_qubits;
+  s->chi = chi;
+  s->n_inst = n_inst;
+  s->dtype = dtype;
+  s->trunc = trunc;
+  s->esz = dtype == NNE_C64 ? 8 : 16;
+  const int n = n_qubits;
+  s->dims.assign(n + 1, 1);
+  s->cap.assign(n + 1, 1);
+  for (int k = 1; k < n; ++k) {
+    long long c = chi;
+    long long p = 1;
+    for (int i = 0; i < k && p < c; ++i) p *= 4;
+    c = std::min(c, p);
+    p = 1;
+    for (int i = 0; i < n - k && p < c; ++i) p *= 4;
+    c = std::min(c, p);
+    s->cap[k] = (int)c;
+    s->dmax = std::max(s->dmax, (int)c);
+  }
+  auto fail = [&](nne_status rc) {
+    s->mem.release();
+    delete s;
+    return rc;
+  };
+  // site arena
+  size_t total = 0;
+  std::vector<size_t> off(n);
+  s->sstride.resize(n);
+  for (int k = 0; k < n; ++k) {
+    s->sstride[k] = (long long)s->cap[k] * 4 * s->cap[k + 1];
+    off[k] = total;
+    total += (size_t)s->sstride[k] * n_inst * s->esz;
+    total = (total + 255) & ~size_t(255);
+  }
+  void* arena = nullptr;
+  nne_status rc = s->mem.alloc(&arena, total);
+  if (rc != NNE_OK) return fail(rc);
+  s->site.resize(n);
+  for (int k = 0; k < n; ++k) s->site[k] = reinterpret_cast<char*>(arena) + off[k];
+  // initial product state |b><b| : s = 3 b
+  {
+    std::vector<char> host(total, 0);
+    for (int k = 0; k < n; ++k) {
+      const int b = init_bits ? (init_bits[k] ? 1 : 0) : 0;
+      for (int i = 0; i < n_inst; ++i) {
+        char* p = host.data() + off[k] + (size_t)i * s->sstride[k] * s->esz + (size_t)(3 * b) * s->esz;
+        if (dtype == NNE_C64) {
+          const float one = 1.0f;
+          memcpy(p, &one, sizeof(float));
+        } else {
+          const double one = 1.0;
+          memcpy(p, &one, sizeof(double));
+        }
+      }
+    }
+    cudaError_t e = cudaMemcpy(arena, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpy", __FILE__, __LINE__));
+  }
+  // scalars
+  void* p = nullptr;
+  if ((rc = s->mem.alloc(&p, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64)) != NNE_OK)
+    return fail(rc);
+  cudaMemset(p, 0, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64);
+  s->d_lognorm = reinterpret_cast<double*>(p);
+  s->d_logfid = s->d_lognorm + n_inst;
+  s->d_scale = s->d_logfid + n_inst;
+  s->d_parts = s->d_scale + n_inst;
+  s->d_err = reinterpret_cast<int*>(s->d_parts + 2 * (size_t)n_inst * PARTS);
+  // workspaces
+  const long long D = s->dmax, N4 = 4 * D;
+  s->sX = N4 * N4;
+  s->sH = N4 * N4;
+  s->sU = N4 * D;
+  s->sT = N4 * N4;
+  s->sR = N4 * D > D * D ? N4 * D : D * D;
+  if ((rc = s->mem.alloc(&s->X, (size_t)s->sX * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  if ((rc = s->mem.alloc(&s->H, (size_t)s->sH * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  if ((rc = s->mem.alloc(&s->U, (size_t)s->sU * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  if ((rc = s->mem.alloc(&s->T, (size_t)s->sT * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  if ((rc = s->mem.alloc(&s->Rm, (size_t)s->sR * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  const EighWork ew = eigh_workspace((int)N4, (int)D);
+  const size_t rsz = s->esz / 2;
+  if ((rc = s->mem.alloc(&s->eig_cx, (size_t)ew.cx_elems * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  if ((rc = s->mem.alloc(&s->eig_re, (size_t)ew.re_elems * n_inst * rsz + 256)) != NNE_OK) return fail(rc);
+  if ((rc = s->mem.alloc(&s->eig_u8, (size_t)ew.u8_elems * n_inst)) != NNE_OK) return fail(rc);
+  const QrWork qw = qr_workspace((int)N4, (int)N4);
+  if ((rc = s->mem.alloc(&s->qr_ws, (size_t)qw.cx_elems * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  // sweep buffers
+  if ((rc = s->mem.alloc(&p, sizeof(int) * (n + 1))) != NNE_OK) return fail(rc);
+  s->d_dims = reinterpret_cast<int*>(p);
+  if ((rc = s->mem.alloc(&p, sizeof(void*) * n)) != NNE_OK) return fail(rc);
+  s->d_site = reinterpret_cast<void**>(p);
+  if ((rc = s->mem.alloc(&p, sizeof(long long) * n)) != NNE_OK) return fail(rc);
+  s->d_stride = reinterpret_cast<long long*>(p);
+  if ((rc = s->mem.alloc(&p, sizeof(double) * 2 * 2 * (size_t)(n + 1) * D * n_inst)) != NNE_OK) return fail(rc);
+  s->d_env = reinterpret_cast<double*>(p);
+  if ((rc = s->mem.alloc(&p, sizeof(double) * 2 * (size_t)(n + 1) * n_inst)) != NNE_OK) return fail(rc);
+  s->d_envscale = reinterpret_cast<double*>(p);
+  {
+    std::vector<void*> hs(s->site.begin(), s->site.end());
+    cudaError_t e = cudaMemcpy(s->d_site, hs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_stride, s->sstride.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpy", __FILE__, __LINE__));
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaDeviceSynchronize", __FILE__, __LINE__));
+  *out = s;
+  return NNE_OK;
+}
+
+void nne_destroy_state(nne_state* st) {
+  if (!st) return;
+  DeviceGuard g(st->ctx->device);
+  cudaStreamSynchronize(st->ctx->stream);
+  st->mem.release();
+  delete st;
+}
+
+nne_status nne_set_sketch(nne_state* st, const void* omega, int rows, int cols, int power_iters) {
+  (void)st; (void)omega; (void)rows; (void)cols; (void)power_iters;
+  return set_error(NNE_ERR_UNIMPL, "randomized truncation not built yet");
+}
+
+nne_status nne_apply_layer(nne_state* st, int n_gates, const int* left_qubit, const void* G, int direction) {
+  if (!st || n_gates < 0 || (n_gates > 0 && (!left_qubit || !G)) || (direction != 1 && direction != -1))
+    return set_error(NNE_ERR_ARG, "nne_apply_layer: bad arguments");
+  for (int g = 0; g < n_gates; ++g)
+    if (left_qubit[g] < 0 || left_qubit[g] > st->n - 2)
+      return set_error(NNE_ERR_ARG, "gate %d: left qubit %d out of range", g, left_qubit[g]);
+  DeviceGuard dg(st->ctx->device);
+  const double* Gd = reinterpret_cast<const double*>(G);
+  const long long sG = (long long)n_gates * 256;   // complex elements between instances
+  for (int g = 0; g < n_gates; ++g) {
+    nne_status rc = st->dtype == NNE_C64 ? gate_step<float>(st, left_qubit[g], Gd + 2LL * 256 * g, sG, direction)
+                                         : gate_step<double>(st, left_qubit[g], Gd + 2LL * 256 * g, sG, direction);
+    if (rc != NNE_OK) return rc;
+  }
+  return NNE_OK;
+}
+
+nne_status nne_truncate(nne_state* st, int chi_new, double* log_fid_out) {
+  if (!st || chi_new < 1 || chi_new > st->chi) return set_error(NNE_ERR_ARG, "nne_truncate: bad arguments");
+  DeviceGuard dg(st->ctx->device);
+  std::vector<double> before(st->n_inst), after(st->n_inst);
+  NNE_CUDA_TRY(cudaMemcpyAsync(before.data(), st->d_logfid, sizeof(double) * st->n_inst, cudaMemcpyDeviceToHost,
+                               st->ctx->stream));
+  nne_status rc = st->dtype == NNE_C64 ? compress<float>(st, chi_new) : compress<double>(st, chi_new);
+  if (rc != NNE_OK) return rc;
+  NNE_CUDA_TRY(cudaMemcpyAsync(after.data(), st->d_logfid, sizeof(double) * st->n_inst, cudaMemcpyDeviceToHost,
+                               st->ctx->stream));
+  if ((rc = read_err(st)) != NNE_OK) return rc;
+  if (log_fid_out)
+    for (int i = 0; i < st->n_inst; ++i) log_fid_out[i] = after[i] - before[i];
+  return NNE_OK;
+}
+
+nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* re_out, double* im_out,
+                      double* log_fid_out) {
+  if (!st || n_obs < 0 || (n_obs > 0 && (!paulis || !re_out || !im_out)))
+    return set_error(NNE_ERR_ARG, "nne_expect: bad arguments");
+  DeviceGuard dg(st->ctx->device);
+  const int n = st->n;
+  std::vector<int> first(std::max(n_obs, 1), -1), last(std::max(n_obs, 1), -1);
+  for (int o = 0; o < n_obs; ++o)
+    for (int k = 0; k < n; ++k) {
+      const int p = paulis[(size_t)o * n + k];
+      if (p > 3) return set_error(NNE_ERR_ARG, "pauli code %d at (%d, %d)", p, o, k);
+      if (p) {
+        if (first[o] < 0) first[o] = k;
+        last[o] = k;
+      }
+    }
+  cudaStream_t s = st->ctx->stream;
+  void *dp = nullptr, *df = nullptr, *dl = nullptr, *dout = nullptr;
+  const size_t bp = (size_t)std::max(n_obs, 1) * n, bf = sizeof(int) * std::max(n_obs, 1),
+               bo = sizeof(double) * 2 * (size_t)std::max(n_obs, 1) * st->n_inst;
+  NNE_CUDA_TRY(cudaMalloc(&dp, bp));
+  NNE_CUDA_TRY(cudaMalloc(&df, bf));
+  NNE_CUDA_TRY(cudaMalloc(&dl, bf));
+  NNE_CUDA_TRY(cudaMalloc(&dout, bo));
+  std::vector<double> hout(2 * (size_t)std::max(n_obs, 1) * st->n_inst);
+  cudaError_t e = cudaMemcpyAsync(st->d_dims, st->dims.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_obs > 0) e = cudaMemcpyAsync(dp, paulis, (size_t)n_obs * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(df, first.data(), bf, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dl, last.data(), bf, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = st->dtype == NNE_C64
+            ? expect_sweep<float>(s, n, st->d_dims, (const void* const*)st->d_site, st->d_stride, st->n_inst, st->dmax,
+                                  n_obs, (const uint8_t*)dp, (const int*)df, (const int*)dl, st->d_env,
+                                  st->d_envscale, (double*)dout)
+            : expect_sweep<double>(s, n, st->d_dims, (const void* const*)st->d_site, st->d_stride, st->n_inst,
+                                   st->dmax, n_obs, (const uint8_t*)dp, (const int*)df, (const int*)dl, st->d_env,
+                                   st->d_envscale, (double*)dout);
+  if (e == cudaSuccess && n_obs > 0)
+    e = cudaMemcpyAsync(hout.data(), dout, sizeof(double) * 2 * (size_t)n_obs * st->n_inst, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && log_fid_out)
+    e = cudaMemcpyAsync(log_fid_out, st->d_logfid, sizeof(double) * st->n_inst, cudaMemcpyDeviceToHost, s);
+  nne_status rc = NNE_OK;
+  if (e != cudaSuccess) rc = set_cuda_error(e, "nne_expect", __FILE__, __LINE__);
+  if (rc == NNE_OK) rc = read_err(st);
+  cudaFree(dp);
+  cudaFree(df);
+  cudaFree(dl);
+  cudaFree(dout);
+  if (rc != NNE_OK) return rc;
+  for (int i = 0; i < st->n_inst; ++i)
+    for (int o = 0; o < n_obs; ++o) {
+      re_out[(size_t)i * n_obs + o] = hout[2 * ((size_t)i * n_obs + o)];
+      im_out[(size_t)i * n_obs + o] = hout[2 * ((size_t)i * n_obs + o) + 1];
+    }
+  return NNE_OK;
+}
+
+nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, const double* values,
+                           const double* log_fid, int n_obs, int method, int degree, double lambda_star,
+                           const double* y_zero, double* out, int32_t* per_obs_status) {
+  if (!ctx || n_lambda < 1 || n_lambda > 64 || !lambdas || !values || n_obs < 0 || !out || !per_obs_status ||
+      method < 0 || method > 2 || (method == NNE_FIT_POLY && (degree < 1 || degree > 15)))
+    return set_error(NNE_ERR_ARG, "nne_extrapolate: bad arguments");
+  if (n_obs == 0) return NNE_OK;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = ctx->stream;
+  double *dl = nullptr, *dv = nullptr, *df = nullptr, *dy = nullptr, *dout = nullptr;
+  int* dst = nullptr;
+  NNE_CUDA_TRY(cudaMalloc(&dl, sizeof(double) * n_lambda));
+  NNE_CUDA_TRY(cudaMalloc(&dv, sizeof(double) * n_lambda * (size_t)n_obs));
+  NNE_CUDA_TRY(cudaMalloc(&df, sizeof(double) * n_lambda));
+  NNE_CUDA_TRY(cudaMalloc(&dy, sizeof(double) * (size_t)n_obs));
+  NNE_CUDA_TRY(cudaMalloc(&dout, sizeof(double) * (size_t)n_obs));
+  NNE_CUDA_TRY(cudaMalloc(&dst, sizeof(int) * (size_t)n_obs));
+  cudaError_t e = cudaMemcpyAsync(dl, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dv, values, sizeof(double) * n_lambda * (size_t)n_obs, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && log_fid) e = cudaMemcpyAsync(df, log_fid, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && y_zero) e = cudaMemcpyAsync(dy, y_zero, sizeof(double) * n_obs, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = extrapolate_fit(s, n_lambda, dl, dv, log_fid ? df : nullptr, n_obs, method, degree, lambda_star,
+                        y_zero ? dy : nullptr, dout, dst);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * n_obs, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(per_obs_status, dst, sizeof(int) * n_obs, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  nne_status rc = e == cudaSuccess ? NNE_OK : set_cuda_error(e, "nne_extrapolate", __FILE__, __LINE__);
+  cudaFree(dl);
+  cudaFree(dv);
+  cudaFree(df);
+  cudaFree(dy);
+  cudaFree(dout);
+  cudaFree(dst);
+  return rc;
+}
+
+nne_status nne_sync(nne_state* st) {
+  if (!st) return set_error(NNE_ERR_ARG, "null state");
+  DeviceGuard dg(st->ctx->device);
+  return read_err(st);
+}
+
+nne_status nne_state_info(nne_state* st, int* dims_out, int* centre_out, double* log_norm_out, double* log_fid_out) {
+  if (!st) return set_error(NNE_ERR_ARG, "null state");
+  DeviceGuard dg(st->ctx->device);
+  if (log_norm_out)
+    NNE_CUDA_TRY(cudaMemcpyAsync(log_norm_out, st->d_lognorm, sizeof(double) * st->n_inst, cudaMemcpyDeviceToHost,
+                                 st->ctx->stream));
+  if (log_fid_out)
+    NNE_CUDA_TRY(cudaMemcpyAsync(log_fid_out, st->d_logfid, sizeof(double) * st->n_inst, cudaMemcpyDeviceToHost,
+                                 st->ctx->stream));
+  nne_status rc = read_err(st);
+  if (rc != NNE_OK) return rc;
+  if (dims_out)
+    for (int k = 0; k <= st->n; ++k) dims_out[k] = st->dims[k];
+  if (centre_out) *centre_out = st->centre;
+  return NNE_OK;
+}
+
+nne_status nne_state_read_site(nne_state* st, int inst, int k, void* host_out, size_t cap_bytes) {
+  if (!st || inst < 0 || inst >= st->n_inst || k < 0 || k >= st->n || !host_out)
+    return set_error(NNE_ERR_ARG, "nne_state_read_site: bad arguments");
+  DeviceGuard dg(st->ctx->device);
+  const size_t bytes = (size_t)st->dims[k] * 4 * st->dims[k + 1] * st->esz;
+  if (cap_bytes < bytes) return set_error(NNE_ERR_ARG, "buffer too small: %zu < %zu", cap_bytes, bytes);
+  NNE_CUDA_TRY(cudaMemcpyAsync(host_out, st->site[k] + (size_t)inst * st->sstride[k] * st->esz, bytes,
+                               cudaMemcpyDeviceToHost, st->ctx->stream));
+  return read_err(st);
+}
+
+nne_status nne_state_write_site(nne_state* st, int inst, int k, int dl, int dr, const void* host_in) {
+  if (!st || inst < 0 || inst >= st->n_inst || k < 0 || k >= st->n || !host_in || dl < 1 || dr < 1 ||
+      dl > st->cap[k] || dr > st->cap[k + 1])
+    return set_error(NNE_ERR_ARG, "nne_state_write_site: bad arguments (dims above capacity?)");
+  DeviceGuard dg(st->ctx->device);
+  const size_t bytes = (size_t)dl * 4 * dr * st->esz;
+  NNE_CUDA_TRY(cudaMemcpyAsync(st->site[k] + (size_t)inst * st->sstride[k] * st->esz, host_in, bytes,
+                               cudaMemcpyHostToDevice, st->ctx->stream));
+  st->dims[k] = dl;
+  st->dims[k + 1] = dr;
+  return read_err(st);
+}
+
+nne_status nne_state_set_centre(nne_state* st, int centre) {
+  if (!st || centre < 0 || centre >= st->n) return set_error(NNE_ERR_ARG, "bad centre");
+  st->centre = centre;
+  return NNE_OK;
+}
+
+}  // extern "C"

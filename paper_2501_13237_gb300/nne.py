@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libnne (include/nne.h): argument marshalling only.
+
+Every arithmetic step runs in the CUDA kernels of libnne.so.  Loading fails
+loudly when the library is missing: there is no CPU or PyTorch fallback.
+Device buffers are torch CUDA tensors (plumbing only); host buffers are
+numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnne.so")
+
+OK, PENDING = 0, 1
+ERR = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NOCONV", -5: "TIMEOUT", -6: "NOFIT", -7: "UNIMPL"}
+C64, C128 = 0, 1
+TRUNC_EXACT, TRUNC_RSVD = 0, 1
+FIT_POLY, FIT_EXP_LOGLIN, FIT_EXP3 = 0, 1, 2
+ERR_NOFIT = -6
+
+# Every symbol include/nne.h declares.
+SYMBOLS = (
+    "nne_ctx_create", "nne_ctx_destroy", "nne_ctx_bytes_in_use", "nne_last_error", "nne_build_superops",
+    "nne_create_state", "nne_destroy_state", "nne_set_sketch", "nne_apply_layer", "nne_truncate", "nne_expect",
+    "nne_extrapolate", "nne_sync", "nne_state_info", "nne_state_read_site", "nne_state_write_site",
+    "nne_state_set_centre",
+)
+
+
+class NNEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libnne status {status} ({ERR.get(status, '?')}): {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libnne.so and declare signatures (raises if the library is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with python -m paper_2501_13237_gb300.build "
+                           "(no CPU fallback exists)")
+    L = C.CDLL(path)
+    vp, i32, dbl, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    P = C.POINTER
+    sig = {
+        "nne_ctx_create": (i32, [i32, vp, sz, P(vp)]),
+        "nne_ctx_destroy": (None, [vp]),
+        "nne_ctx_bytes_in_use": (sz, [vp]),
+        "nne_last_error": (C.c_char_p, []),
+        "nne_build_superops": (i32, [vp, i32, vp, i32, vp, vp]),
+        "nne_create_state": (i32, [vp, i32, i32, i32, i32, i32, vp, P(vp)]),
+        "nne_destroy_state": (None, [vp]),
+        "nne_set_sketch": (i32, [vp, vp, i32, i32, i32]),
+        "nne_apply_layer": (i32, [vp, i32, vp, vp, i32]),
+        "nne_truncate": (i32, [vp, i32, vp]),
+        "nne_expect": (i32, [vp, i32, vp, vp, vp, vp]),
+        "nne_extrapolate": (i32, [vp, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp]),
+        "nne_sync": (i32, [vp]),
+        "nne_state_info": (i32, [vp, vp, vp, vp, vp]),
+        "nne_state_read_site": (i32, [vp, i32, i32, vp, sz]),
+        "nne_state_write_site": (i32, [vp, i32, i32, i32, i32, vp]),
+        "nne_state_set_centre": (i32, [vp, i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != OK:
+        raise NNEError(status, load().nne_last_error().decode(errors="replace"))
+
+
+def _hptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None, hbm_budget_bytes: int = 0):
+        L = load()
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        _check(L.nne_ctx_create(device, C.c_void_p(int(stream.cuda_stream)), hbm_budget_bytes, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().nne_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bytes_in_use(self) -> int:
+        return int(load().nne_ctx_bytes_in_use(self.h))
+
+    def build_superops(self, U: np.ndarray, rates: np.ndarray):
+        """a1: U (g,4,4) complex128, rates (n_inst,4) -> device tensor (n_inst, g, 16, 16) complex128."""
+        import torch
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        rates = np.ascontiguousarray(rates, dtype=np.float64).reshape(-1, 4)
+        g, ni = U.shape[0], rates.shape[0]
+        G = torch.empty((ni, g, 16, 16), dtype=torch.complex128, device=f"cuda:{self.device}")
+        _check(load().nne_build_superops(self.h, g, _hptr(U), ni, _hptr(rates), C.c_void_p(_dptr(G))))
+        return G
+
+    def extrapolate(self, lambdas, values, log_fid=None, method=FIT_EXP_LOGLIN, degree=2, lambda_star=1.0,
+                    y_zero=None):
+        """a8: values (n_lambda, n_obs) -> (estimates[n_obs], status[n_obs])."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        vals = np.ascontiguousarray(values, dtype=np.float64)
+        if vals.ndim == 1:
+            vals = vals[:, None]
+        nl, no = vals.shape
+        lf = None if log_fid is None else np.ascontiguousarray(log_fid, dtype=np.float64)
+        yz = None if y_zero is None else np.ascontiguousarray(y_zero, dtype=np.float64)
+        out = np.zeros(no)
+        st = np.zeros(no, np.int32)
+        _check(load().nne_extrapolate(self.h, nl, _hptr(lam), _hptr(vals), _hptr(lf), no, method, degree,
+                                      float(lambda_star), _hptr(yz), _hptr(out), _hptr(st)))
+        return out, st
+
+
+class State:
+    def __init__(self, ctx: Context, n: int, chi: int, n_inst: int, dtype: int = C64, trunc: int = TRUNC_EXACT,
+                 bits: Optional[Sequence[int]] = None):
+        self.ctx, self.n, self.chi, self.n_inst, self.dtype = ctx, n, chi, n_inst, dtype
+        b = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)
+        h = C.c_void_p()
+        _check(load().nne_create_state(ctx.h, n, chi, n_inst, dtype, trunc, _hptr(b), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            load().nne_destroy_state(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_sketch(self, omega: np.ndarray, power_iters: int):
+        om = np.ascontiguousarray(omega, dtype=np.complex64 if self.dtype == C64 else np.complex128)
+        _check(load().nne_set_sketch(self.h, _hptr(om), om.shape[0], om.shape[1], power_iters))
+
+    def apply_layer(self, left_qubits: Sequence[int], G, direction: int):
+        """G: device complex128 tensor (n_inst, n_gates, 16, 16) for exactly these gates, in order."""
+        qs = np.ascontiguousarray(left_qubits, dtype=np.int32)
+        _check(load().nne_apply_layer(self.h, int(qs.size), _hptr(qs), C.c_void_p(_dptr(G)), int(direction)))
+
+    def truncate(self, chi_new: int) -> np.ndarray:
+        out = np.zeros(self.n_inst)
+        _check(load().nne_truncate(self.h, chi_new, _hptr(out)))
+        self.chi = chi_new
+        return out
+
+    def expect(self, paulis: np.ndarray):
+        """paulis (n_obs, n) uint8 -> (values complex (n_inst, n_obs), log_fid (n_inst))."""
+        p = np.ascontiguousarray(paulis, dtype=np.uint8)
+        no = p.shape[0]
+        re = np.zeros((self.n_inst, no))
+        im = np.zeros((self.n_inst, no))
+        lf = np.zeros(self.n_inst)
+        _check(load().nne_expect(self.h, no, _hptr(p), _hptr(re), _hptr(im), _hptr(lf)))
+        return re + 1j * im, lf
+
+    def sync(self):
+        _check(load().nne_sync(self.h))
+
+    def info(self):
+        dims = np.zeros(self.n + 1, np.int32)
+        centre = C.c_int()
+        ln = np.zeros(self.n_inst)
+        lf = np.zeros(self.n_inst)
+        _check(load().nne_state_info(self.h, _hptr(dims), C.byref(centre), _hptr(ln), _hptr(lf)))
+        return dims, centre.value, ln, lf
+
+    def read_site(self, inst: int, k: int) -> np.ndarray:
+        dims, _, _, _ = self.info()
+        dt = np.complex64 if self.dtype == C64 else np.complex128
+        out = np.zeros((dims[k], 4, dims[k + 1]), dt)
+        _check(load().nne_state_read_site(self.h, inst, k, _hptr(out), out.nbytes))
+        return out
+
+    def write_site(self, inst: int, k: int, M: np.ndarray):
+        dt = np.complex64 if self.dtype == C64 else np.complex128
+        M = np.ascontiguousarray(M, dtype=dt)
+        _check(load().nne_state_write_site(self.h, inst, k, M.shape[0], M.shape[2], _hptr(M)))
+
+    def set_centre(self, c: int):
+        _check(load().nne_state_set_centre(self.h, c))

@@ -1,0 +1,48 @@
+"""Brickwork schedule on top of the C ABI: which gates go into which
+nne_apply_layer call, in which direction.  No arithmetic happens here.
+
+Schedule (a reading of the paper, which fixes none): layer t holds the gates
+(q, q+1) with q = t mod 2 (mod 2); even layers are applied left to right,
+odd layers right to left, so the orthogonality centre snakes along the
+chain and each layer needs no extra centre sweep.
+"""
+from __future__ import annotations
+
+from typing import List, Tuple
+
+import numpy as np
+
+from . import nne
+
+
+def layer_plan(circuit) -> List[Tuple[List[int], np.ndarray, int]]:
+    """Per layer: (left qubits in application order, unitaries in that order, direction)."""
+    plan = []
+    for t, (qs, us) in enumerate(zip(circuit.layers, circuit.unitaries)):
+        if len(qs) == 0:
+            continue
+        if t % 2 == 0:
+            plan.append((list(qs), np.asarray(us), +1))
+        else:
+            plan.append((list(qs)[::-1], np.asarray(us)[::-1], -1))
+    return plan
+
+
+def build_layer_superops(ctx: nne.Context, circuit, rates: np.ndarray):
+    """Device superoperators for every layer (a1), in application order."""
+    return [(qs, ctx.build_superops(us, rates), d) for qs, us, d in layer_plan(circuit)]
+
+
+def evolve(state: nne.State, layers) -> None:
+    for qs, G, d in layers:
+        state.apply_layer(qs, G, d)
+
+
+def emulate(ctx: nne.Context, circuit, rates: np.ndarray, chi: int, paulis: np.ndarray, dtype: int = nne.C64,
+            trunc: int = nne.TRUNC_EXACT, bits=None, layers=None):
+    """Run one circuit at all noise levels (one instance per row of rates).
+    Returns (state, <P> (n_inst, n_obs) complex, log F (n_inst))."""
+    st = nne.State(ctx, circuit.n, chi, rates.shape[0], dtype, trunc, bits)
+    evolve(st, layers if layers is not None else build_layer_superops(ctx, circuit, rates))
+    vals, lf = st.expect(paulis)
+    return st, vals, lf

@@ -1,0 +1,170 @@
+"""GPU parity: every step of the hot path through the C ABI against the oracle.
+
+Tolerances: the complex128 path must agree with the oracle within 1e-10 on
+untruncated runs and 1e-8 at the same chi truncation; the complex64 path
+within 1e-4 (single-precision arithmetic with float64 norms)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import channels, dense, fit as ofit, mps
+from tests.gpu_util import rand_c, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-10}     # dtype -> tolerance (C64, C128)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    from paper_2501_13237_gb300 import nne
+    return nne.Context(0)
+
+
+def test_superops_match_oracle(ctx):
+    rng = np.random.default_rng(0)
+    U = np.stack([wl.haar_u4(rng) for _ in range(7)])
+    rates = np.array([[1e-3, 5e-4, 2e-4, 0.0], [0.3, 0.1, 0.05, 0.02], [0, 0, 0, 0.4]])
+    G = ctx.build_superops(U, rates).cpu().numpy()
+    for i, r in enumerate(rates):
+        for g in range(U.shape[0]):
+            assert np.abs(G[i, g] - channels.gate_superop(U[g], r)).max() < 1e-13
+
+
+@pytest.mark.parametrize("dtype", [1, 0])
+@pytest.mark.parametrize("dl,dm,dr,chi,direction", [
+    (24, 40, 20, 50, +1), (24, 40, 20, 50, -1),      # truncating, ragged shapes
+    (3, 9, 5, 64, +1), (3, 9, 5, 64, -1),            # r = 4 dl or 4 dr: identity branch
+    (16, 64, 16, 64, +1), (7, 33, 30, 37, -1),       # several tiles, odd tails
+])
+def test_single_gate_step(ctx, dtype, dl, dm, dr, chi, direction):
+    """One gate step on sites (3, 4) of an 8-site chain (capacities
+    min(chi, 4^k, 4^(8-k)) admit the shapes) vs the oracle's two-site update."""
+    from paper_2501_13237_gb300 import nne
+    rng = np.random.default_rng(dl * 1000 + dr + (direction > 0))
+    A = rand_c(rng, (dl, 4, dm))
+    B = rand_c(rng, (dm, 4, dr))
+    n, q = 8, 3
+    st = nne.State(ctx, n, chi, 2, dtype)
+    for inst in range(2):
+        st.write_site(inst, q, A)
+        st.write_site(inst, q + 1, B)
+    # a single step touches only the pair once the centre is on it
+    st.set_centre(q if direction > 0 else q + 1)
+    U = np.stack([wl.haar_u4(rng)])
+    rates = np.array([[0.02, 0.01, 0.0, 0.0], [0.1, 0.0, 0.03, 0.0]])
+    G = ctx.build_superops(U, rates)
+    st.apply_layer([q], G, direction)
+    dims, centre, ln, lf = st.info()
+    Gh = G.cpu().numpy()
+    tol = TOL[dtype]
+    for inst in range(2):
+        left, right, f, nrm, s = mps.two_site_update(A, B, Gh[inst, 0], chi, direction)
+        L = st.read_site(inst, q).astype(np.complex128)
+        R = st.read_site(inst, q + 1).astype(np.complex128)
+        got = np.einsum("asc,ctb->astb", L, R).reshape(4 * dl, 4 * dr)
+        ref = np.einsum("asc,ctb->astb", left, right).reshape(4 * dl, 4 * dr)
+        assert np.abs(got - ref).max() < tol * max(1.0, np.abs(ref).max())
+        assert abs(lf[inst] - math.log(f)) < tol
+        assert abs(ln[inst] - math.log(nrm)) < tol
+        r = L.shape[2]
+        if direction > 0:
+            Lm = L.reshape(-1, r)
+            assert np.abs(Lm.conj().T @ Lm - np.eye(r)).max() < 10 * tol
+        else:
+            Rm = R.reshape(r, -1)
+            assert np.abs(Rm @ Rm.conj().T - np.eye(r)).max() < 10 * tol
+    assert centre == (q + 1 if direction > 0 else q)
+    assert dims[q + 1] == min(chi, 4 * dl, 4 * dr)
+    st.close()
+
+
+def run_gpu(ctx, w, rates, chi, dtype, paulis):
+    from paper_2501_13237_gb300 import runner
+    st, vals, lf = runner.emulate(ctx, w.circuit, rates, chi, paulis, dtype, bits=w.bits())
+    st.close()
+    return vals, lf
+
+
+@pytest.mark.parametrize("dtype", [1, 0])
+def test_exact8_untruncated_vs_dense(ctx, dtype):
+    w = wl.exact8()
+    rates = w.rate_table()
+    paulis = wl.pauli_codes(w.observables, w.n)
+    vals, lf = run_gpu(ctx, w, rates, w.chi, dtype, paulis)
+    for i, lam in enumerate(w.lambdas):
+        rho = dense.run(w.circuit, rates[i])
+        ref = np.array([dense.expect(rho, ob, w.n) for ob in w.observables])
+        assert np.abs(vals[i] - ref).max() < TOL[dtype]
+        assert abs(lf[i]) < TOL[dtype]
+    # quadratic fit to lambda* = 1 on the device vs the oracle fit on the same data
+    from paper_2501_13237_gb300 import nne
+    est, st = ctx.extrapolate(w.lambdas, vals.real, lf, method=nne.FIT_POLY, degree=2, lambda_star=1.0)
+    ref, rst = ofit.extrapolate(ofit.M_POLY, w.lambdas, vals.real, 1.0, degree=2)
+    assert (st == 0).all() and np.abs(est - ref).max() < 1e-10
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 1e-4)])
+@pytest.mark.parametrize("n,depth,chi,seed", [(10, 10, 16, 3), (9, 8, 12, 4)])
+def test_truncated_vs_oracle_mps(ctx, dtype, tol, n, depth, chi, seed):
+    c = wl.brickwork_circuit(n, depth, seed)
+    noise = wl.NoiseModel(depol2=0.02, amp_damp=0.01, dephase=0.01)
+    lams = (1.0, 2.0, 3.0)
+    rates = np.stack([noise.rates(l) for l in lams])
+    obs = wl.obs_z(n) + wl.obs_xx(n) + [((0, "Y"), (1, "X"), (2, "Z"))]
+    paulis = wl.pauli_codes(obs, n)
+
+    class W:
+        pass
+    w = W()
+    w.circuit = c
+    w.bits = lambda: None
+    vals, lf = run_gpu(ctx, w, rates, chi, dtype, paulis)
+    for i in range(len(lams)):
+        ref_st = mps.run(c, rates[i], chi)
+        ref = ref_st.expect_codes(paulis)
+        assert np.abs(vals[i] - ref).max() < tol, (i, np.abs(vals[i] - ref).max())
+        assert abs(lf[i] - ref_st.log_fid) < tol * max(1.0, abs(ref_st.log_fid))
+        assert ref_st.log_fid < -1e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 1e-4)])
+def test_compression_sweep_vs_oracle(ctx, dtype, tol):
+    from paper_2501_13237_gb300 import nne, runner
+    n = 8
+    c = wl.brickwork_circuit(n, 6, 21)
+    rates = np.array([[0.01, 0.005, 0.0, 0.0]])
+    paulis = wl.pauli_codes(wl.obs_z(n) + wl.obs_zz(n), n)
+    st, _, _ = runner.emulate(ctx, c, rates, 64, paulis, dtype)
+    dl = st.truncate(6)
+    vals, lf = st.expect(paulis)
+    ref_st = mps.run(c, rates[0], 64)
+    before = ref_st.log_fid
+    ref_st.truncate(6)
+    ref = ref_st.expect_codes(paulis)
+    assert np.abs(vals[0] - ref).max() < tol
+    assert abs(dl[0] - (ref_st.log_fid - before)) < tol * 10
+    st.close()
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+def test_fit_kernel_vs_oracle(ctx, method):
+    rng = np.random.default_rng(7 + method)
+    lams = np.array([1.0, 1.5, 2.0, 3.0, 4.0, 6.0])
+    n_obs = 40
+    a = rng.uniform(-1, 1, n_obs)
+    b = rng.uniform(0.0, 0.6, n_obs)
+    cst = rng.uniform(-0.05, 0.05, n_obs) * (method == 2)
+    vals = a[None, :] * np.exp(-b[None, :] * lams[:, None]) + cst[None, :]
+    vals = vals * (1 + 0.02 * rng.standard_normal(vals.shape))
+    vals[:, 3] = [0.1, -0.2, 0.05, -0.1, 0.3, -0.01]      # sign changes: criteria 2-3 / fallback
+    vals[:, 4] = [1e-12, 2e-12, 0.2, 0.1, 0.05, 0.02]     # criterion 2
+    log_fid = np.log(np.array([0.2, 0.5, 0.9, 0.995, 0.999, 0.9999]))
+    est, st = ctx.extrapolate(lams, vals, log_fid, method=method, degree=2, lambda_star=1.0)
+    ref, rst = ofit.extrapolate(method, lams, vals, 1.0, log_fid=log_fid, degree=2)
+    assert (st == rst).all()
+    tol = 1e-10 if method != 2 else 1e-7
+    assert np.abs(est - ref).max() < tol * max(1.0, np.abs(ref).max()), np.abs(est - ref).max()
