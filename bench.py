@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the NZNE hot path on GB300: noisy VMPO gate steps at chi = 512.
+
+Workload: n = 100 qubits, 1D brickwork of Haar-random U(4) gates (seed 0),
+every gate followed by two-qubit depolarizing p = 5e-4*lambda, amplitude
+damping gamma = 1e-3*lambda and dephasing 5e-4*lambda on both qubits, 8 noise
+levels lambda = 1..8 run as 8 instances of one state, chi = 512, complex64
+with the randomized range finder truncation (k = chi + 64, one power
+iteration), observables all <Z_i> and <X_i X_i+1>, weighted log-linear
+extrapolation (exponential fallback) to lambda* = 1.  Synthetic inputs from
+workloads/ (no datasets).
+
+One step = two brickwork layers of the saturated regime (99 gates x 8
+instances = 792 two-qubit gate+truncation steps, every bond at chi = 512)
+followed by the expectation sweep over all 199 observables and the fit.
+The state is first evolved through the layers in which the bond dimension
+is still growing (untimed set-up); steps then continue the evolution layer
+after layer.  The state (~6.7 GB) is larger than L2, so no flush is needed.
+
+value      gate steps per second, device-resident inputs (U, rates on HBM),
+           CUDA events on the library's stream, max over ranks.
+e2e        the same metric with the step's inputs copied from pinned host
+           memory and <P>, log F and the fit read back every step.
+roofline   the dominant kernel class from live CUDA-event timing inside the
+           timed region (nne_prof_collect), achieved = algorithmic flops
+           per launch / average launch time.
+cpu_baseline / --impl reference: the CPU oracle (NumPy, float64) timed on a
+           bounded sample: full-size gate steps at chi = 512 on the host cores.
+
+Multi-GPU: replicas only (each rank runs its own instance of the job with its
+own circuit seed, no data-path collective; scaling "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np
+
+CHI = 512
+OVERSAMPLE = 64
+POWER_ITERS = 1
+LAYERS_PER_STEP = 2
+SATURATE_LAYERS = 6          # bond dims 4, 16, 64, 256, 512 reached by layer 5
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "_fallback": True}
+
+
+class ClockSampler:
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_steps(n_steps: int, chi: int = CHI, seed: int = 0):
+    """Time oracle gate steps at full size (random bulk site tensors, chi x 4 x chi)."""
+    import workloads as wl
+    from oracle import channels, mps
+    rng = np.random.default_rng(seed)
+    A = (rng.standard_normal((chi, 4, chi)) + 1j * rng.standard_normal((chi, 4, chi))) / math.sqrt(2)
+    B = (rng.standard_normal((chi, 4, chi)) + 1j * rng.standard_normal((chi, 4, chi))) / math.sqrt(2)
+    G = channels.gate_superop(wl.haar_u4(rng), wl.n100().noise.rates(1.0))
+    t0 = time.perf_counter()
+    for i in range(n_steps):
+        mps.two_site_update(A, B, G, chi, +1 if i % 2 == 0 else -1)
+    return time.perf_counter() - t0
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(int(i.get("num_threads", 1)) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        cpu_oracle_steps(1)
+    dt = cpu_oracle_steps(args.steps)
+    v = args.steps / dt
+    cores = threads_used()
+    line = {"metric": "2q gate+truncation steps/s at chi=512", "value": v, "unit": "gate_steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "n100_d30_chi512_8lambda", "sample": "bulk gate steps chi=512 (X 2048x2048)"},
+            "cpu_baseline": {"value": v, "unit": "gate_steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} bulk gate steps at chi=512, NumPy/LAPACK float64"},
+            "e2e": {"value": v, "unit": "gate_steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", action="store_true", help="print the per-kernel-class breakdown to stderr")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import workloads as wl
+    from paper_2501_13237_gb300 import nne, runner
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    w = wl.n100(seed=rank)
+    rates = w.rate_table()
+    n_inst = rates.shape[0]
+    paulis = wl.pauli_codes(w.observables, w.n)
+    plan = runner.layer_plan(w.circuit)
+    ctx = nne.Context(local)
+    st = nne.State(ctx, w.n, CHI, n_inst, nne.C64, nne.TRUNC_RSVD, w.bits())
+    st.set_sketch(wl.gaussian_sketch(4 * CHI, CHI + OVERSAMPLE, 1234).astype(np.complex64), POWER_ITERS)
+
+    dev = f"cuda:{local}"
+    U_dev = [torch.from_numpy(np.ascontiguousarray(us)).to(dev) for _, us, _ in plan]
+    U_pin = [torch.from_numpy(np.ascontiguousarray(us)).pin_memory() for _, us, _ in plan]
+    rates_dev = torch.from_numpy(rates).to(dev)
+    rates_pin = torch.from_numpy(rates).pin_memory()
+    G_buf = [torch.empty((n_inst, len(qs), 16, 16), dtype=torch.complex128, device=dev) for qs, _, _ in plan]
+    lams = np.array(w.lambdas)
+
+    # set-up: evolve through the growing-bond layers
+    for li in range(SATURATE_LAYERS):
+        qs, _, d = plan[li]
+        st.apply_layer(qs, ctx.build_superops(U_dev[li], rates_dev, out=G_buf[li]), d)
+    st.sync()
+    cursor = [SATURATE_LAYERS]
+
+    def next_layers():
+        out = []
+        for _ in range(LAYERS_PER_STEP):
+            li = cursor[0]
+            out.append(li)
+            cursor[0] = cursor[0] + 1 if cursor[0] + 1 < len(plan) else SATURATE_LAYERS
+        return out
+
+    gates_per_step = 0
+    h2d = d2h = 0
+
+    def step(host_inputs: bool):
+        nonlocal gates_per_step, h2d, d2h
+        gates = 0
+        b_in = 0
+        for li in next_layers():
+            qs, _, d = plan[li]
+            if host_inputs:
+                G = ctx.build_superops(U_pin[li].numpy(), rates_pin.numpy(), out=G_buf[li])
+                b_in += U_pin[li].numel() * 16 + rates_pin.numel() * 8
+            else:
+                G = ctx.build_superops(U_dev[li], rates_dev, out=G_buf[li])
+            st.apply_layer(qs, G, d)
+            gates += len(qs) * n_inst
+        vals, lf = st.expect(paulis)
+        est, status = ctx.extrapolate(lams, vals.real, lf, method=nne.FIT_EXP_LOGLIN, lambda_star=w.lambda_star)
+        gates_per_step = gates
+        if host_inputs:
+            h2d = b_in + paulis.nbytes + vals.real.nbytes + lf.nbytes + lams.nbytes
+            d2h = vals.real.nbytes * 2 + lf.nbytes + est.nbytes + status.nbytes
+        return est
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(host_inputs: bool, K: int, prof: bool = False):
+        stream = ctx.stream
+        barrier()
+        if prof:
+            nne.prof_collect()
+            nne.prof_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = nne.kernel_launches()
+        e0.record(stream)
+        for _ in range(K):
+            step(host_inputs)
+        e1.record(stream)
+        barrier()
+        launches = nne.kernel_launches() - l0
+        pr = None
+        if prof:
+            nne.prof_enable(False)
+            pr = nne.prof_collect()
+        ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, pr
+
+    for _ in range(args.warmup):
+        step(False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches, prof = timed(False, args.steps, prof=True)
+    clk = clocks.stop()
+    ms_e2e, _, _ = timed(True, 1)
+
+    value = gates_per_step * args.steps * world / (ms / 1e3)
+    e2e = gates_per_step * world / (ms_e2e / 1e3)
+
+    # roofline for the dominant kernel class
+    pk = peaks()
+    dominant = max(prof.items(), key=lambda kv: kv[1][0])
+    prof_summary = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
+    roof = roofline(dominant, prof, pk)
+    cpu = None
+    if rank == 0:
+        n_cpu = 3
+        dt = cpu_oracle_steps(n_cpu)
+        cpu = {"value": n_cpu / dt, "unit": "gate_steps/s", "cores": threads_used(), "kind": "oracle",
+               "sample": f"{n_cpu} bulk gate steps at chi=512 (X 2048x2048 complex128, LAPACK SVD)"}
+    if args.profile and rank == 0:
+        for k, (t, c, wk) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+            if c:
+                sys.stderr.write(f"  {k:18s} {t:10.2f} ms  {c:7d} launches  {100 * t / max(ms, 1e-9):5.1f}%\n")
+    if rank == 0:
+        line = {"metric": "2q gate+truncation steps/s at chi=512", "value": value, "unit": "gate_steps/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+                "data": "synthetic",
+                "config": {"workload": "n100_d30_chi512_8lambda", "chi": CHI, "n": w.n, "n_lambda": n_inst,
+                           "truncation": f"randomized range finder k=chi+{OVERSAMPLE}, q={POWER_ITERS}",
+                           "step": f"{LAYERS_PER_STEP} saturated brickwork layers ({gates_per_step} gate steps) "
+                                   "+ 199-observable sweep + fit",
+                           "l2": "inputs larger than L2 (state ~6.7 GB)", "parallelism": f"replicas{world}"},
+                "e2e": {"value": e2e, "unit": "gate_steps/s", "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "kernel_classes_ms": prof_summary}
+        print(json.dumps(line), flush=True)
+    st.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# FP32 SIMT peak of GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz max SM clock.
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# TF32 dense tensor peak: measured bf16 x nominal TF32/bf16 ratio (1.1 / 2.25).
+TF32_RATIO = 1.1 / 2.25
+
+
+def roofline(dominant, prof, pk):
+    """Roofline entry of the dominant kernel class, from live CUDA-event timing.
+
+    GEMM class: achieved = algorithmic real flops of every GEMM launch in the
+    timed region (8 M N K per complex GEMM, recorded by the library per launch)
+    / the class's summed launch time; peak = FP32 SIMT FMA peak."""
+    name, (t_ms, count, work) = dominant
+    if count == 0 or t_ms <= 0:
+        return None
+    out = {"kernel": name, "launches": count, "avg_launch_ms": t_ms / count, "traffic": None}
+    if name == "gemm" and work > 0:
+        achieved = work / (t_ms / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_SIMT_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"})
+    else:
+        out.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None})
+    return out
+
+
+if __name__ == "__main__":
+    main()

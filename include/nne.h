@@ -94,9 +94,10 @@ const char* nne_last_error(void);
  *   ampdamp  K0 = diag(1, sqrt(1-gamma)), K1 = sqrt(gamma)|0><1|, on both qubits
  *   dephase  sqrt(1-p) I, sqrt(p) Z on both qubits
  *   depol1   sqrt(1-p) I, sqrt(p/3){X,Y,Z} on both qubits
- * U     host, n_gates x 4 x 4 complex128 (row-major, basis |b_q b_{q+1}>, b_q
- *       the more significant bit).
- * rates host, n_inst x 4 doubles; every strength in [0, 1] (depol2 <= 16/15).
+ * U     n_gates x 4 x 4 complex128 (row-major, basis |b_q b_{q+1}>, b_q the
+ *       more significant bit), in host or device memory (detected).
+ * rates n_inst x 4 doubles in host or device memory; every strength in
+ *       [0, 1] (depol2 <= 16/15).  Ranges are checked only for host rates.
  * G_out device, n_inst x n_gates x 256 complex128.
  * Computed in float64 on the device; enqueued on the context stream. */
 nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_inst,
@@ -163,6 +164,11 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
                            double lambda_star, const double* y_zero, double* out,
                            int32_t* per_obs_status);
 
+/* Return a state to its initial product state |b><b| without reallocating:
+ * bond dimensions 1, centre 0, log-norm and log F 0.  init_bits host uint8[n],
+ * or NULL for the bits given at creation.  Enqueued on the context stream. */
+nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits);
+
 /* Wait for the state's enqueued work; returns the first device-side error. */
 nne_status nne_sync(nne_state* st);
 
@@ -177,6 +183,23 @@ nne_status nne_state_info(nne_state* st, int* dims_out, int* centre_out, double*
 nne_status nne_state_read_site(nne_state* st, int inst, int k, void* host_out, size_t cap_bytes);
 nne_status nne_state_write_site(nne_state* st, int inst, int k, int dl, int dr, const void* host_in);
 nne_status nne_state_set_centre(nne_state* st, int centre);
+
+/* Instrumentation (no counterpart in the paper).
+ * nne_kernel_launches: number of CUDA kernels this library has launched in
+ *   the process so far (monotone counter).
+ * nne_prof_enable: when on, every launch records a CUDA event pair on its
+ *   stream, grouped by kernel class; nne_prof_collect synchronises on those
+ *   events, writes total milliseconds, launch counts and algorithmic work
+ *   (real flops for the GEMM class, 0 where not tracked) per class (arrays of
+ *   n_classes, any may be NULL) and clears the record.  Returns the number of
+ *   classes.
+ *   Classes: 0 GEMM, 1 superoperator epilogue, 2 tridiagonal reduction,
+ *   3 bisection, 4 inverse iteration, 5 back-transform, 6 QR factor,
+ *   7 QR form-Q, 8 elementwise/norms, 9 environment sweep, 10 observable
+ *   sweep, 11 superoperator build, 12 fit. */
+long long nne_kernel_launches(void);
+void nne_prof_enable(int on);
+int nne_prof_collect(double* ms_out, long long* count_out, double* work_out, int n_classes);
 
 #ifdef __cplusplus
 }

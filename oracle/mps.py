@@ -32,6 +32,18 @@ layers left to right, odd layers right to left.
 Expectation values (Sec. 2.2.3, <O>_lambda; exact contraction of the tensor
 network): <P> = Tr(P rho~) / Tr(rho~) with per-site vectors v_P[s] = P[j, i].
 
+Gauge convention (shared with the GPU path so that site tensors are unique):
+QR factors have a real non-negative R diagonal; every truncation isometry
+(columns ordered by decreasing weight) has each column scaled so its column
+sum is real and non-negative.  Observables do not depend on it; the
+randomized variant below does (its sketch acts in the current bond basis).
+
+Randomized variant (a design choice of the GPU path, not the paper's): the
+kept subspace may instead come from the randomized range finder with a
+given sketch matrix (range_finder_isometry); it equals the SVD truncation
+whenever the sketch covers the rank bound, and otherwise keeps a subspace
+whose captured weight is at most the optimal one.
+
 Pins (tests/test_oracle_mps.py): untruncated runs equal the dense simulator
 to 1e-12 (n <= 8); lambda = 0 equals the statevector; truncated runs equal an
 independent brute-force emulation that applies each gate to the full dense
@@ -55,10 +67,30 @@ PAULI_VEC = {
 }
 
 
+def fix_columns(W: np.ndarray) -> np.ndarray:
+    """Gauge convention for an isometry: each column times conj(sum)/|sum| so that
+    its column sum is real and non-negative (unchanged when the sum is zero)."""
+    s = W.sum(axis=0)
+    a = np.abs(s)
+    ph = np.where(a > 0, np.conj(s) / np.where(a > 0, a, 1.0), 1.0)
+    return W * ph[None, :]
+
+
+def qr_fixed(M: np.ndarray):
+    """Reduced QR with the gauge convention R_jj real and non-negative."""
+    Q, R = np.linalg.qr(M)
+    d = np.diagonal(R)
+    a = np.abs(d)
+    ph = np.where(a > 0, d / np.where(a > 0, a, 1.0), 1.0)
+    return Q * ph[None, :], np.conj(ph)[:, None] * R
+
+
 class VMPO:
-    def __init__(self, n: int, chi: int, bits=None):
+    def __init__(self, n: int, chi: int, bits=None, sketch: np.ndarray = None, power_iters: int = 0):
         self.n = n
         self.chi = chi
+        self.sketch = sketch
+        self.power_iters = power_iters
         bits = [0] * n if bits is None else [int(b) for b in bits]
         self.M: List[np.ndarray] = []
         for b in bits:
@@ -76,7 +108,7 @@ class VMPO:
         """Make site k left-isometric and push R into site k+1."""
         A = self.M[k]
         cl, _, cr = A.shape
-        Q, R = np.linalg.qr(A.reshape(cl * 4, cr))
+        Q, R = qr_fixed(A.reshape(cl * 4, cr))
         self.M[k] = Q.reshape(cl, 4, Q.shape[1])
         self.M[k + 1] = np.einsum("ij,jsb->isb", R, self.M[k + 1])
 
@@ -84,7 +116,7 @@ class VMPO:
         """Make site k right-isometric and push L into site k-1."""
         B = self.M[k]
         cl, _, cr = B.shape
-        Q, R = np.linalg.qr(B.reshape(cl, 4 * cr).conj().T)    # B^dagger = Q R  ->  B = R^dagger Q^dagger
+        Q, R = qr_fixed(B.reshape(cl, 4 * cr).conj().T)        # B^dagger = Q R  ->  B = R^dagger Q^dagger
         self.M[k] = Q.conj().T.reshape(Q.shape[1], 4, cr)
         self.M[k - 1] = np.einsum("asj,ji->asi", self.M[k - 1], R.conj().T)
 
@@ -99,7 +131,8 @@ class VMPO:
     # ------------------------------------------------------------- gate step
     def gate(self, q: int, G: np.ndarray, direction: int):
         self.move_centre(q if direction > 0 else q + 1)
-        left, right, f, nrm, s = two_site_update(self.M[q], self.M[q + 1], G, self.chi, direction)
+        left, right, f, nrm, s = two_site_update(self.M[q], self.M[q + 1], G, self.chi, direction,
+                                                 self.sketch, self.power_iters)
         self.M[q], self.M[q + 1] = left, right
         self.centre = q + 1 if direction > 0 else q
         self.log_norm += math.log(nrm)
@@ -122,13 +155,15 @@ class VMPO:
         for k in range(self.n - 1):
             A = self.M[k]
             cl, _, cr = A.shape
-            U, S, Vh = np.linalg.svd(A.reshape(cl * 4, cr), full_matrices=False)
+            Am = A.reshape(cl * 4, cr)
+            U, S, Vh = np.linalg.svd(Am, full_matrices=False)
             r = min(chi_new, S.size)
             total = float(np.sum(S ** 2))
             kept = float(np.sum(S[:r] ** 2))
-            C = S[:r, None] * Vh[:r]
+            Ur = fix_columns(U[:, :r])
+            C = Ur.conj().T @ Am
             nrm = float(np.linalg.norm(C))
-            self.M[k] = U[:, :r].reshape(cl, 4, r)
+            self.M[k] = Ur.reshape(cl, 4, r)
             self.M[k + 1] = np.einsum("ij,jsb->isb", C / nrm, self.M[k + 1])
             self.log_norm += math.log(nrm)
             self.log_fid += math.log(kept / total)
@@ -178,26 +213,73 @@ def theta_superop(A: np.ndarray, B: np.ndarray, G: np.ndarray) -> np.ndarray:
     return thetap.reshape(cl * 4, 4 * cr)
 
 
-def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direction: int):
+def range_finder_isometry(A: np.ndarray, r: int, omega: np.ndarray, q: int) -> np.ndarray:
+    """Top-r left singular subspace of A (n x m) by the randomized range finder:
+    Y = A Omega (k columns), q power iterations A (A^H Q) with re-orthonormalisation,
+    Rayleigh-Ritz on C = (Q^H A)(Q^H A)^H, W = Q * (top-r eigenvectors of C)
+    (Halko, Martinsson & Tropp 2011, Algs. 4.4 and 5.1).  When k >= n the sketch
+    spans the whole space and the exact top-r eigenvectors of A A^H are returned."""
+    n, m = A.shape
+    k = omega.shape[1]
+    if k >= n or k < r:
+        ev, V = np.linalg.eigh(A @ A.conj().T)
+        return fix_columns(V[:, ::-1][:, :r])
+    Q, _ = np.linalg.qr(A @ omega[:m, :k])
+    for _ in range(q):
+        Z, _ = np.linalg.qr(A.conj().T @ Q)
+        Q, _ = np.linalg.qr(A @ Z)
+    Bm = Q.conj().T @ A
+    ev, V = np.linalg.eigh(Bm @ Bm.conj().T)
+    return fix_columns(Q @ V[:, ::-1][:, :r])
+
+
+def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direction: int,
+                    sketch: np.ndarray = None, power_iters: int = 0):
     """One subcircuit on a pair in canonical form (steps 2-6 of the module header).
 
+    With a sketch matrix the kept subspace comes from the randomized range finder
+    (range_finder_isometry) instead of the exact SVD; the split, normalisation and
+    f_l bookkeeping are the same.
     Returns (new_left, new_right, f, norm_of_kept_part, singular_values)."""
     cl, cr = A.shape[0], B.shape[2]
     X = theta_superop(A, B, G)
-    U, S, Vh = np.linalg.svd(X, full_matrices=False)
     r = min(chi, 4 * cl, 4 * cr)
+    if (direction > 0 and r == 4 * cl) or (direction < 0 and r == 4 * cr):
+        # nothing can be cut on the isometry's side: keep the identity basis
+        S = np.linalg.svd(X, compute_uv=False)
+        nrm = float(np.linalg.norm(X))
+        if direction > 0:
+            return np.eye(4 * cl, dtype=X.dtype).reshape(cl, 4, r), (X / nrm).reshape(r, 4, cr), 1.0, nrm, S
+        return (X / nrm).reshape(cl, 4, r), np.eye(4 * cr, dtype=X.dtype).reshape(r, 4, cr), 1.0, nrm, S
+    if sketch is not None:
+        S = np.linalg.svd(X, compute_uv=False)
+        total = float(np.sum(np.abs(X) ** 2))
+        if direction > 0:
+            Ur = range_finder_isometry(X, r, sketch, power_iters)
+            C = Ur.conj().T @ X
+            kept = float(np.sum(np.abs(C) ** 2))
+            nrm = math.sqrt(kept)
+            return Ur.reshape(cl, 4, r), (C / nrm).reshape(r, 4, cr), kept / total, nrm, S
+        Vr = range_finder_isometry(X.conj().T, r, sketch, power_iters)
+        C = X @ Vr
+        kept = float(np.sum(np.abs(C) ** 2))
+        nrm = math.sqrt(kept)
+        return (C / nrm).reshape(cl, 4, r), Vr.conj().T.reshape(r, 4, cr), kept / total, nrm, S
+    U, S, Vh = np.linalg.svd(X, full_matrices=False)
     total = float(np.sum(S ** 2))
     kept = float(np.sum(S[:r] ** 2))
     if direction > 0:
-        C = S[:r, None] * Vh[:r]
+        Ur = fix_columns(U[:, :r])
+        C = Ur.conj().T @ X
         nrm = float(np.linalg.norm(C))
-        left = U[:, :r].reshape(cl, 4, r)
+        left = Ur.reshape(cl, 4, r)
         right = (C / nrm).reshape(r, 4, cr)
     else:
-        C = U[:, :r] * S[None, :r]
+        Vr = fix_columns(Vh[:r].conj().T)
+        C = X @ Vr
         nrm = float(np.linalg.norm(C))
         left = (C / nrm).reshape(cl, 4, r)
-        right = Vh[:r].reshape(r, 4, cr)
+        right = Vr.conj().T.reshape(r, 4, cr)
     return left, right, kept / total, nrm, S
 
 
@@ -208,9 +290,9 @@ def superops_for(circuit, rates) -> List[np.ndarray]:
             for us in circuit.unitaries]
 
 
-def run(circuit, rates, chi: int, bits=None, Gs=None) -> VMPO:
+def run(circuit, rates, chi: int, bits=None, Gs=None, sketch=None, power_iters: int = 0) -> VMPO:
     """Emulate a brickwork circuit at one noise level with the snake schedule."""
-    st = VMPO(circuit.n, chi, bits)
+    st = VMPO(circuit.n, chi, bits, sketch, power_iters)
     Gs = superops_for(circuit, rates) if Gs is None else Gs
     for t, (qs, G) in enumerate(zip(circuit.layers, Gs)):
         if len(qs) == 0:

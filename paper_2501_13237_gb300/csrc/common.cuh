@@ -65,6 +65,24 @@ struct Batched {
   } while (0)
 
 namespace nne {
+// Kernel classes for launch accounting / event timing (nne_prof_collect).
+enum ProfClass {
+  K_GEMM = 0, K_SUPEROP_APPLY = 1, K_TRIDIAG = 2, K_BISECT = 3, K_INVITER = 4, K_BACKTRANSFORM = 5,
+  K_QR_FACTOR = 6, K_QR_FORMQ = 7, K_ELEMWISE = 8, K_SWEEP_ENV = 9, K_SWEEP_OBS = 10, K_SUPEROP_BUILD = 11,
+  K_FIT = 12, PROF_CLASSES = 16
+};
+class ProfScope {
+ public:
+  // work: algorithmic flops (GEMM) or bytes (sweeps) of these launches, 0 if not tracked
+  ProfScope(cudaStream_t st, int cls, int kernels = 1, double work = 0.0);
+  ~ProfScope();
+ private:
+  cudaStream_t st_;
+  int cls_;
+  bool on_;
+  double work_;
+  cudaEvent_t a_, b_;
+};
 nne_status set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 nne_status set_error(nne_status s, const char* fmt, ...);
 }  // namespace nne

@@ -79,6 +79,7 @@ cudaError_t cgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<R> 
                   long long sA, int lda, const cx<R>* B, long long sB, int ldb, cx<R> beta, cx<R>* C,
                   long long sC, int ldc, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  ProfScope ps(st, K_GEMM, 1, 8.0 * M * N * (double)K * batch);
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   if (opA == OP_N && opB == OP_N)
     cgemm_kernel<R, OP_N, OP_N><<<grid, 256, 0, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC, ldc);
@@ -127,6 +128,7 @@ template <typename R>
 cudaError_t apply_superop(cudaStream_t st, cx<R>* X, long long sX, int dl, int dr, const double* G, long long sG,
                           int batch) {
   const long long work = (long long)dl * dr;
+  ProfScope ps(st, K_SUPEROP_APPLY);
   dim3 grid((unsigned)((work + 255) / 256), 1, batch);
   apply_superop_kernel<R><<<grid, 256, 0, st>>>(X, sX, dl, dr, G, sG);
   return cudaGetLastError();
@@ -158,6 +160,7 @@ __global__ void __launch_bounds__(256) sumsq_partial_kernel(const cx<R>* X, long
 template <typename R>
 cudaError_t sumsq_partial(cudaStream_t st, const cx<R>* X, long long sX, long long count, double* out, int parts,
                           int batch) {
+  ProfScope ps(st, K_ELEMWISE);
   dim3 grid(parts, batch);
   sumsq_partial_kernel<R><<<grid, 256, 0, st>>>(X, sX, count, out, parts);
   return cudaGetLastError();
@@ -200,6 +203,7 @@ __global__ void scale_kernel(cx<R>* X, long long sX, long long count, const doub
 
 template <typename R>
 cudaError_t scale_batched(cudaStream_t st, cx<R>* X, long long sX, long long count, const double* scale, int batch) {
+  ProfScope ps(st, K_ELEMWISE);
   int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
   scale_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, count, scale);
@@ -232,6 +236,7 @@ __global__ void transpose_kernel(const cx<R>* X, long long sX, int rows, int col
 template <typename R>
 cudaError_t transpose(cudaStream_t st, bool conj_, const cx<R>* X, long long sX, int rows, int cols, int ldx,
                       cx<R>* Y, long long sY, int ldy, int batch) {
+  ProfScope ps(st, K_ELEMWISE);
   dim3 grid((cols + 31) / 32, (rows + 31) / 32, batch);
   dim3 block(32, 8);
   if (conj_)
@@ -250,6 +255,7 @@ __global__ void conj_inplace_kernel(cx<R>* X, long long sX, long long count) {
 
 template <typename R>
 cudaError_t conj_inplace(cudaStream_t st, cx<R>* X, long long sX, long long count, int batch) {
+  ProfScope ps(st, K_ELEMWISE);
   int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
   conj_inplace_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, count);
@@ -270,6 +276,7 @@ __global__ void identity_kernel(cx<R>* X, long long sX, int rows, int cols) {
 template <typename R>
 cudaError_t identity(cudaStream_t st, cx<R>* X, long long sX, int rows, int cols, int batch) {
   const long long count = (long long)rows * cols;
+  ProfScope ps(st, K_ELEMWISE);
   int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
   identity_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, rows, cols);
@@ -287,9 +294,87 @@ __global__ void copy_kernel(const cx<R>* X, long long sX, cx<R>* Y, long long sY
 template <typename R>
 cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y, long long sY, long long count,
                          int batch) {
+  ProfScope ps(st, K_ELEMWISE);
   int blocks = (int)std::min<long long>((count + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
   copy_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, Y, sY, count);
+  return cudaGetLastError();
+}
+
+// Gauge fixing of an isometry W (n x r, ld r): column j is multiplied by
+// conj(sum_i W[i][j]) / |sum_i W[i][j]| so that its column sum is real and
+// non-negative (a zero sum leaves the column unchanged).
+template <typename R>
+__global__ void __launch_bounds__(256) fix_columns_kernel(cx<R>* Wb, long long sW, int n, int r) {
+  __shared__ double red[2][8];
+  const int j = blockIdx.x, z = blockIdx.y;
+  cx<R>* W = Wb + z * sW;
+  double sr = 0, si = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const cx<R> w = W[(long long)i * r + j];
+    sr += w.re;
+    si += w.im;
+  }
+  sr = warp_sum_r(sr);
+  si = warp_sum_r(si);
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sr; red[1][threadIdx.x >> 5] = si; }
+  __syncthreads();
+  double tr = 0, ti = 0;
+  for (int w = 0; w < 8; ++w) { tr += red[0][w]; ti += red[1][w]; }
+  const double a = sqrt(tr * tr + ti * ti);
+  if (!(a > 0)) return;
+  const cx<R> ph = mk<R>((R)(tr / a), (R)(-ti / a));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) W[(long long)i * r + j] = W[(long long)i * r + j] * ph;
+}
+
+template <typename R>
+cudaError_t fix_columns(cudaStream_t st, cx<R>* W, long long sW, int n, int r, int batch) {
+  if (r <= 0 || n <= 0) return cudaSuccess;
+  ProfScope ps(st, K_ELEMWISE);
+  fix_columns_kernel<R><<<dim3(r, batch), 256, 0, st>>>(W, sW, n, r);
+  return cudaGetLastError();
+}
+
+// QR gauge: R_jj real and non-negative.  Q column j *= d_j, R row j *= conj(d_j),
+// d_j = R_jj / |R_jj| (1 when R_jj = 0).  Q (m x k, ld k), R (k x n, ld n).
+template <typename R>
+__global__ void __launch_bounds__(256) fix_qr_kernel(cx<R>* Qb, long long sQ, int m, int k, cx<R>* Rb, long long sR,
+                                                      int n) {
+  const int j = blockIdx.x, z = blockIdx.y;
+  cx<R>* Q = Qb + z * sQ;
+  cx<R>* Rm = Rb + z * sR;
+  const cx<R> rjj = Rm[(long long)j * n + j];
+  const double a = sqrt((double)rjj.re * rjj.re + (double)rjj.im * rjj.im);
+  if (!(a > 0)) return;
+  const cx<R> d = mk<R>((R)(rjj.re / a), (R)(rjj.im / a));
+  const cx<R> dc = conj(d);
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) Q[(long long)i * k + j] = Q[(long long)i * k + j] * d;
+  for (int c = j + threadIdx.x; c < n; c += blockDim.x) Rm[(long long)j * n + c] = Rm[(long long)j * n + c] * dc;
+}
+
+template <typename R>
+cudaError_t fix_qr(cudaStream_t st, cx<R>* Q, long long sQ, int m, int k, cx<R>* Rm, long long sR, int n, int batch) {
+  if (k <= 0) return cudaSuccess;
+  ProfScope ps(st, K_ELEMWISE);
+  fix_qr_kernel<R><<<dim3(k, batch), 256, 0, st>>>(Q, sQ, m, k, Rm, sR, n);
+  return cudaGetLastError();
+}
+
+// Product state |b><b| on every site and instance: bond dims 1, M[0][s][0] = [s == 3 b].
+template <typename R>
+__global__ void product_state_kernel(int n, void* const* site, const long long* stride, const uint8_t* bits) {
+  const int k = blockIdx.x, z = blockIdx.y, s = threadIdx.x;
+  if (s >= 4) return;
+  cx<R>* M = reinterpret_cast<cx<R>*>(site[k]) + z * stride[k];
+  M[s] = mk<R>(s == 3 * (bits[k] ? 1 : 0) ? R(1) : R(0), R(0));
+}
+
+template <typename R>
+cudaError_t product_state(cudaStream_t st, int n, void* const* d_site, const long long* d_stride, int n_inst,
+                          const uint8_t* d_bits) {
+  ProfScope ps(st, K_ELEMWISE);
+  product_state_kernel<R><<<dim3(n, n_inst), 32, 0, st>>>(n, d_site, d_stride, d_bits);
   return cudaGetLastError();
 }
 
@@ -303,13 +388,17 @@ cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y
                                     int, int);                                                                   \
   template cudaError_t conj_inplace<R>(cudaStream_t, cx<R>*, long long, long long, int);                         \
   template cudaError_t identity<R>(cudaStream_t, cx<R>*, long long, int, int, int);                              \
-  template cudaError_t copy_batched<R>(cudaStream_t, const cx<R>*, long long, cx<R>*, long long, long long, int);
+  template cudaError_t copy_batched<R>(cudaStream_t, const cx<R>*, long long, cx<R>*, long long, long long, int); \
+  template cudaError_t product_state<R>(cudaStream_t, int, void* const*, const long long*, int, const uint8_t*); \
+  template cudaError_t fix_columns<R>(cudaStream_t, cx<R>*, long long, int, int, int);                          \
+  template cudaError_t fix_qr<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, int, int);
 
 NNE_INST_BLAS(float)
 NNE_INST_BLAS(double)
 
 cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, int parts, int batch,
                         double* scale, double* log_norm, double* log_fid, int* err) {
+  ProfScope ps(st, K_ELEMWISE);
   finish_gate_kernel<<<(batch + 127) / 128, 128, 0, st>>>(kept_parts, total_parts, parts, batch, scale, log_norm,
                                                           log_fid, err);
   return cudaGetLastError();

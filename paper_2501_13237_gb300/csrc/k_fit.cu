@@ -216,6 +216,7 @@ cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, 
                             const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
                             const double* d_yzero, double* d_out, int* d_status) {
   if (n_obs <= 0) return cudaSuccess;
+  ProfScope ps(st, K_FIT);
   fit_kernel<<<(n_obs + 63) / 64, 64, 0, st>>>(n_lambda, d_lam, d_vals, d_logfid, n_obs, method, degree, lambda_star,
                                               d_yzero, d_out, d_status);
   return cudaGetLastError();

@@ -75,10 +75,10 @@ __device__ cx<R> householder(cx<R>* v, int m, double* red) {
 
 // ---------------------------------------------------------------- tridiagonal
 // H (n x n) -> real tridiagonal d, complex subdiagonal e (e[k] = T[k+1][k]);
-// reflector j (length n-j-1) is stored in row j of H, columns j+1..n-1.
+// reflector j (length n-j-1) is stored conjugated in row j of Vh, columns j+1..n-1.
 template <typename R>
 __global__ void __launch_bounds__(256) tridiag_kernel(cx<R>* Hb, long long sH, int n, R* db, cx<R>* eb, int ldde,
-                                                       cx<R>* Pb, double* Kb) {
+                                                       cx<R>* Pb, double* Kb, cx<R>* Vhb, long long sVh) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) tridiag_kernel(cx<R>* Hb, long long sH, i
       w[t] = mk<R>(2 * p.re - twoK * v[t].re, 2 * p.im - twoK * v[t].im);
     }
     if (rank == 0) {
-      cx<R>* rj = H + (long long)j * n + (j + 1);
-      for (int t = tid; t < m; t += nth) rj[t] = v[t];      // keep reflector j for the back-transform
+      cx<R>* rj = Vhb + z * sVh + (long long)j * n + (j + 1);
+      for (int t = tid; t < m; t += nth) rj[t] = conj(v[t]);   // reflector j, conjugated, for the back-transform
     }
     __syncthreads();
     for (int t = gw; t < m; t += GW) {
@@ -334,132 +334,6 @@ __global__ void inviter_kernel(const R* db, const R* eb, int n, int r, int ldde,
   }
 }
 
-// U[row0 + i][c] -= 2 v_i (v^H U[row0.., c]) for one 32-column block; warp w
-// owns rows congruent to w mod 8 (absolute), so only `red` is shared.
-template <typename R>
-__device__ __forceinline__ void reflect_colblock(cx<R>* U, int ldu, int c, bool active, const cx<R>* v, int row0,
-                                                 int len, cx<R> (*red)[32]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int first = row0 + ((warp - row0 % 8) + 8) % 8;
-  cx<R> p = mk<R>(0, 0);
-  if (active)
-    for (int row = first; row < row0 + len; row += 8) fmac_(p, v[row - row0], U[(long long)row * ldu + c]);
-  red[warp][lane] = p;
-  __syncthreads();
-  cx<R> s = mk<R>(0, 0);
-  for (int w = 0; w < 8; ++w) s = s + red[w][lane];
-  __syncthreads();
-  if (active) {
-    const cx<R> s2 = mk<R>(2 * s.re, 2 * s.im);
-    for (int row = first; row < row0 + len; row += 8) {
-      const cx<R> vi = v[row - row0];
-      cx<R>& u = U[(long long)row * ldu + c];
-      u = u - vi * s2;
-    }
-  }
-}
-
-// U = Q_house D Z for a 32-column block: start from phi_k Z[k][c], apply
-// reflectors n-3 .. 0 (reflector j in row j of H, acting on rows j+1..).
-template <typename R>
-__global__ void __launch_bounds__(256) backtransform_kernel(const cx<R>* Hb, long long sH, int n, int r,
-                                                             const cx<R>* phib, int ldde, const R* Zb, long long sZ,
-                                                             cx<R>* Ub, long long sU) {
-  __shared__ cx<R> red[8][32];
-  const int z = blockIdx.y;
-  const cx<R>* H = Hb + z * sH;
-  const cx<R>* phi = phib + (long long)z * ldde;
-  const R* Z = Zb + z * sZ;
-  cx<R>* U = Ub + z * sU;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + lane;
-  const bool active = c < r;
-  if (active)
-    for (int k = warp; k < n; k += 8) U[(long long)k * r + c] = Z[(long long)k * r + c] * phi[k];
-  for (int j = n - 3; j >= 0; --j) {
-    reflect_colblock(U, r, c, active, H + (long long)j * n + (j + 1), j + 1, n - j - 1, red);
-  }
-}
-
-// ---------------------------------------------------------------- QR
-// Factor A (m x n, row-major) in place: reflector j (length m-j) to V row j;
-// column blocks of 32 owned by CTA (block % CS).  A[j][j] = alpha_j, and
-// A[i][j] = 0 for i > j, so the upper triangle of A is R on exit.
-template <typename R>
-__global__ void __launch_bounds__(256) qr_factor_kernel(cx<R>* Ab, long long sA, int m, int n, cx<R>* Vb,
-                                                         long long sV) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int CS = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
-  const int z = blockIdx.y;
-  cx<R>* A = Ab + z * sA;
-  cx<R>* V = Vb + z * sV;
-  extern __shared__ unsigned char smem_raw[];
-  cx<R>* v = reinterpret_cast<cx<R>*>(smem_raw);
-  __shared__ cx<R> red[8][32];
-  __shared__ double dred[32];
-  const int lane = threadIdx.x & 31;
-  const int nblk = (n + 31) / 32;
-  const int k = min(m, n);
-  for (int j = 0; j < k; ++j) {
-    const int mj = m - j;
-    const int owner = (j / 32) % CS;
-    if (rank == owner) {
-      for (int t = threadIdx.x; t < mj; t += blockDim.x) v[t] = A[(long long)(j + t) * n + j];
-      __syncthreads();
-      const cx<R> alpha = householder(v, mj, dred);
-      for (int t = threadIdx.x; t < mj; t += blockDim.x) {
-        V[(long long)j * m + t] = v[t];
-        A[(long long)(j + t) * n + j] = t == 0 ? alpha : mk<R>(0, 0);
-      }
-      __threadfence();
-    }
-    cluster.sync();
-    if (rank != owner) {
-      for (int t = threadIdx.x; t < mj; t += blockDim.x) v[t] = V[(long long)j * m + t];
-    }
-    __syncthreads();
-    for (int b = rank; b < nblk; b += CS) {
-      if (32 * b + 31 <= j) continue;
-      const int c = 32 * b + lane;
-      reflect_colblock(A, n, c, c > j && c < n, v, j, mj, red);
-      __syncthreads();
-    }
-  }
-}
-
-// Q (m x k, ld = k) = P_0 ... P_{k-1} [I_k; 0] for one 32-column block.
-template <typename R>
-__global__ void __launch_bounds__(256) qr_formq_kernel(const cx<R>* Vb, long long sV, int m, int k, cx<R>* Qb,
-                                                        long long sQ) {
-  __shared__ cx<R> red[8][32];
-  const int z = blockIdx.y;
-  const cx<R>* V = Vb + z * sV;
-  cx<R>* Q = Qb + z * sQ;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = blockIdx.x * 32 + lane;
-  const bool inb = c < k;
-  if (inb)
-    for (int i = warp; i < m; i += 8) Q[(long long)i * k + c] = mk<R>(i == c ? R(1) : R(0), R(0));
-  const int jmax = min(k - 1, blockIdx.x * 32 + 31);
-  for (int j = jmax; j >= 0; --j) {
-    reflect_colblock(Q, k, c, inb && c >= j, V + (long long)j * m, j, m - j, red);
-  }
-}
-
-template <typename R>
-__global__ void qr_extract_r_kernel(const cx<R>* Ab, long long sA, int m, int n, cx<R>* Rb, long long sR) {
-  const int z = blockIdx.y;
-  const cx<R>* A = Ab + z * sA;
-  cx<R>* Rm = Rb + z * sR;
-  const int k = min(m, n);
-  const long long count = (long long)k * n;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
-    const int row = (int)(i / n), col = (int)(i % n);
-    Rm[i] = col >= row ? A[(long long)row * n + col] : mk<R>(0, 0);
-  }
-}
-
 // ---------------------------------------------------------------- launchers
 template <typename K, typename... Args>
 static cudaError_t launch_cluster(K kernel, int cs, int batch, size_t smem, cudaStream_t st, Args... args) {
@@ -491,37 +365,13 @@ static int cluster_size_for(int n) { return n >= 512 ? 8 : (n >= 128 ? 4 : (n >=
 EighWork eigh_workspace(int n, int r) {
   EighWork w;
   const long long qn = std::max(n, r);
-  // cx: e (n), phi (n), P (n), QR reflectors (r x n)
-  w.cx_elems = 3LL * n + (long long)r * n + 32;
+  // cx: e, phi, P (n each), Vh (n x n), WY factors (ceil(n/32) x 32 x 32), W, W2 (32 x r each),
+  //     QR workspace of an n x r matrix
+  w.cx_elems = 3LL * n + (long long)n * n + ((n + 31) / 32) * 1024LL + 64LL * r + qr_workspace(n, r).cx_elems + 32;
   // re: d, eabs (n each), lam (r), Z (n r), L/U0/U1/U2 (4 n r), Kpart (32 doubles = 64 floats)
   w.re_elems = 2LL * n + r + 5LL * n * r + 64 + qn;
   w.u8_elems = (long long)n * r;
   return w;
-}
-
-QrWork qr_workspace(int m, int n) {
-  QrWork w;
-  w.cx_elems = (long long)std::min(m, n) * m;
-  return w;
-}
-
-template <typename R>
-cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, long long sQ, cx<R>* Rout,
-               long long sR, void* cx_ws, int batch) {
-  const int k = std::min(m, n);
-  if (k <= 0 || batch <= 0) return cudaSuccess;
-  cx<R>* V = reinterpret_cast<cx<R>*>(cx_ws);
-  const long long sV = (long long)k * m;
-  const int cs = std::min(cluster_size_for(std::max(m, n)), (n + 31) / 32);
-  cudaError_t e = launch_cluster(qr_factor_kernel<R>, std::max(cs, 1), batch, sizeof(cx<R>) * (size_t)m, st, A, sA,
-                                 m, n, V, sV);
-  if (e != cudaSuccess) return e;
-  if (Rout) {
-    qr_extract_r_kernel<R><<<dim3(64, batch), 256, 0, st>>>(A, sA, m, n, Rout, sR);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  qr_formq_kernel<R><<<dim3((k + 31) / 32, batch), 256, 0, st>>>(V, sV, m, k, Q, sQ);
-  return cudaGetLastError();
 }
 
 template <typename R>
@@ -538,7 +388,12 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
   cx<R>* e = cxb;                                   // batch x n
   cx<R>* phi = e + (long long)batch * n;            // batch x n
   cx<R>* P = phi + (long long)batch * n;            // batch x n
-  cx<R>* qrws = P + (long long)batch * n;           // batch x (r n)
+  cx<R>* Vh = P + (long long)batch * n;             // batch x n x n
+  cx<R>* Tw = Vh + (long long)batch * n * n;        // batch x nb x 1024
+  const int nbw = (n + 31) / 32;
+  cx<R>* W = Tw + (long long)batch * nbw * 1024;    // batch x 32 r
+  cx<R>* W2 = W + (long long)batch * 32 * r;
+  cx<R>* qrws = W2 + (long long)batch * 32 * r;     // QR workspace for batch n x r matrices
   R* d = reb;                                       // batch x n
   R* eabs = d + (long long)batch * n;               // batch x n
   R* lam = eabs + (long long)batch * n;             // batch x r
@@ -550,28 +405,42 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
   double* Kp = reinterpret_cast<double*>(U2 + (long long)batch * n * r + 1);
   Kp = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Kp) + 15) & ~uintptr_t(15));
   (void)w;
-  const int cs = cluster_size_for(n);
-  cudaError_t ce = launch_cluster(tridiag_kernel<R>, cs, batch, 2 * sizeof(cx<R>) * (size_t)n, st, H, sH, n, d, e,
-                                  ldde, P, Kp);
+  cudaError_t ce = cudaMemsetAsync(Vh, 0, sizeof(cx<R>) * (size_t)batch * n * n, st);
   if (ce != cudaSuccess) return ce;
-  tridiag_phases_kernel<R><<<(batch + 63) / 64, 64, 0, st>>>(e, n, ldde, eabs, phi, batch);
+  if (smem_cluster_size<R>(n) > 0) {
+    ce = tridiag_smem<R>(st, H, sH, n, d, e, ldde, Vh, (long long)n * n, batch);
+  } else {
+    const int cs = cluster_size_for(n);
+    ProfScope ps(st, K_TRIDIAG);
+    ce = launch_cluster(tridiag_kernel<R>, cs, batch, 2 * sizeof(cx<R>) * (size_t)n, st, H, sH, n, d, e, ldde, P, Kp,
+                        Vh, (long long)n * n);
+  }
+  if (ce != cudaSuccess) return ce;
+  {
+    ProfScope ps(st, K_ELEMWISE);
+    tridiag_phases_kernel<R><<<(batch + 63) / 64, 64, 0, st>>>(e, n, ldde, eabs, phi, batch);
+  }
   if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
   const int total = batch * r;
-  bisect_kernel<R><<<(total * 32 + 255) / 256, 256, 0, st>>>(d, eabs, n, r, ldde, lam, r, total);
+  {
+    ProfScope ps(st, K_BISECT);
+    bisect_kernel<R><<<(total * 32 + 255) / 256, 256, 0, st>>>(d, eabs, n, r, ldde, lam, r, total);
+  }
   if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
   const long long sS = (long long)n * r;
-  inviter_kernel<R><<<(total + 127) / 128, 128, 0, st>>>(d, eabs, n, r, ldde, lam, r, Z, sS, Ls, U0, U1, U2, u8b,
-                                                         sS, total);
+  {
+    ProfScope ps(st, K_INVITER);
+    inviter_kernel<R><<<(total + 127) / 128, 128, 0, st>>>(d, eabs, n, r, ldde, lam, r, Z, sS, Ls, U0, U1, U2, u8b,
+                                                           sS, total);
+  }
   if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
-  backtransform_kernel<R><<<dim3((r + 31) / 32, batch), 256, 0, st>>>(H, sH, n, r, phi, ldde, Z, sS, U, sU);
-  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  ce = backtransform_wy<R>(st, Vh, (long long)n * n, n, Z, sS, phi, ldde, r, U, sU, Tw, W, W2, batch);
+  if (ce != cudaSuccess) return ce;
   // orthonormalise the eigenvector block (QR; Q written over U)
   return qr<R>(st, U, sU, n, r, U, sU, nullptr, 0, qrws, batch);
 }
 
 #define NNE_INST_LINALG(R)                                                                                       \
-  template cudaError_t qr<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, cx<R>*, long long, \
-                             void*, int);                                                                       \
   template cudaError_t eigh_top<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, void*, void*, \
                                    void*, int, int*);
 NNE_INST_LINALG(float)

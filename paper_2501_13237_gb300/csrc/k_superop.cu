@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) gate_superop_kernel(int n_gates, const do
 
 cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int n_inst, const double* d_rates,
                            double* d_G, double* d_Snoise) {
+  ProfScope ps(st, K_SUPEROP_BUILD, 2);
   noise_superop_kernel<<<n_inst, 256, 0, st>>>(d_rates, d_Snoise);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

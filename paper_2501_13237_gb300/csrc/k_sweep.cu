@@ -179,8 +179,12 @@ template <typename R>
 cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* const* d_site,
                          const long long* d_stride, int n_inst, int max_dim, int n_obs, const uint8_t* d_paulis,
                          const int* d_first, const int* d_last, double* d_env, double* d_envscale, double* d_out) {
-  env_kernel<R><<<dim3(2, n_inst), 256, 0, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  {
+    ProfScope ps(st, K_SWEEP_ENV);
+    env_kernel<R><<<dim3(2, n_inst), 256, 0, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   if (n_obs <= 0) return cudaSuccess;
   const size_t smem = 2 * sizeof(cx<double>) * (size_t)max_dim;
@@ -188,6 +192,7 @@ cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* 
     e = cudaFuncSetAttribute(obs_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  ProfScope ps(st, K_SWEEP_OBS);
   obs_kernel<R><<<dim3(n_obs, n_inst), 256, smem, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale,
                                                         d_paulis, d_first, d_last, n_obs, d_out);
   return cudaGetLastError();

@@ -31,6 +31,15 @@ template <typename R>
 cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y, long long sY, long long count,
                          int batch);
 
+template <typename R>
+cudaError_t product_state(cudaStream_t st, int n, void* const* d_site, const long long* d_stride, int n_inst,
+                          const uint8_t* d_bits);
+
+template <typename R>
+cudaError_t fix_columns(cudaStream_t st, cx<R>* W, long long sW, int n, int r, int batch);
+template <typename R>
+cudaError_t fix_qr(cudaStream_t st, cx<R>* Q, long long sQ, int m, int k, cx<R>* Rm, long long sR, int n, int batch);
+
 // ---- k_linalg.cu
 // Workspace sizes (elements) for eigh_top on n x n matrices with r wanted vectors.
 struct EighWork {
@@ -45,6 +54,16 @@ EighWork eigh_workspace(int n, int r);
 template <typename R>
 cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R>* U, long long sU, void* cx_ws,
                      void* re_ws, void* u8_ws, int batch, int* err);
+
+template <typename R>
+int smem_cluster_size(int n);
+template <typename R>
+cudaError_t tridiag_smem(cudaStream_t st, const cx<R>* H, long long sH, int n, R* d, cx<R>* e, int ldde, cx<R>* Vh,
+                         long long sVh, int batch);
+template <typename R>
+cudaError_t backtransform_wy(cudaStream_t st, const cx<R>* Vh, long long sVh, int n, const R* Z, long long sZ,
+                             const cx<R>* phi, int ldde, int r, cx<R>* U, long long sU, cx<R>* Tw, cx<R>* W,
+                             cx<R>* W2, int batch);
 
 struct QrWork {
   long long cx_elems;

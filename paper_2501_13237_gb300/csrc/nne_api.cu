@@ -34,11 +34,20 @@ nne_status set_cuda_error(cudaError_t e, const char* what, const char* file, int
 
 using namespace nne;
 
+struct ScratchF64 {
+  double* p = nullptr;
+  size_t n = 0;
+};
+
 struct nne_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   size_t budget = 0;
   size_t used = 0;
+  ScratchF64 snoise;   // superoperator-build scratch, grown on demand
+  ~nne_ctx() {
+    if (snoise.p) cudaFree(snoise.p);
+  }
 };
 
 namespace {
@@ -68,6 +77,21 @@ struct DevAlloc {
 };
 
 constexpr int PARTS = 64;   // partial sums per instance for Frobenius norms
+
+ScratchF64& scratch_snoise(nne_ctx* ctx, int n_inst) {
+  const size_t need = 512 * (size_t)n_inst;
+  if (ctx->snoise.n < need) {
+    if (ctx->snoise.p) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->snoise.p);
+    }
+    ctx->snoise.p = nullptr;
+    ctx->snoise.n = 0;
+    if (cudaMalloc(&ctx->snoise.p, need * sizeof(double)) == cudaSuccess) ctx->snoise.n = need;
+    else ctx->snoise.p = nullptr;
+  }
+  return ctx->snoise;
+}
 
 }  // namespace
 
@@ -104,9 +128,13 @@ struct nne_state {
   long long* d_stride = nullptr;
   double* d_env = nullptr;
   double* d_envscale = nullptr;
+  std::vector<uint8_t> bits;
+  uint8_t* d_bits = nullptr;
   // randomized truncation
   void* d_omega = nullptr;
   int omega_rows = 0, omega_cols = 0, power_iters = 0;
+  void* rs_Y = nullptr; void* rs_Z = nullptr; void* rs_C = nullptr; void* rs_W = nullptr;
+  long long rs_sY = 0, rs_sZ = 0, rs_sC = 0, rs_sW = 0;
 };
 
 namespace {
@@ -151,6 +179,7 @@ nne_status qr_right(nne_state* s, int c) {
   cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
   cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
   CTRY(qr<R>(st, M, s->sstride[c], m, dr, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));
+  CTRY(fix_qr<R>(st, Q, s->sT, m, k, Rr, s->sR, dr, s->n_inst));
   CTRY(copy_batched<R>(st, Q, s->sT, M, s->sstride[c], (long long)m * k, s->n_inst));
   // next <- R next
   cx<R>* N = sp<R>(s, c + 1);
@@ -174,6 +203,7 @@ nne_status lq_left(nne_state* s, int c) {
   cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
   cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
   CTRY(qr<R>(st, Mh, s->sU, m, dl, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));          // Q (m x k), R (k x dl)
+  CTRY(fix_qr<R>(st, Q, s->sT, m, k, Rr, s->sR, dl, s->n_inst));
   CTRY(transpose<R>(st, true, Q, s->sT, m, k, k, M, s->sstride[c], m, s->n_inst));       // site c = Q^H (k x m)
   cx<R>* P = sp<R>(s, c - 1);
   cx<R>* tmp = reinterpret_cast<cx<R>*>(s->H);
@@ -198,21 +228,59 @@ nne_status move_centre(nne_state* s, int target) {
 }
 
 // Top-r left (dir > 0) or right (dir < 0) singular subspace of X[z] as an
-// isometry: exact eigenvectors of the Gram matrix, or the randomized range
-// finder with Rayleigh-Ritz.  Writes W (rows x r, ld r) into s->U.
+// isometry W (n_side x r, ld r) in s->U.
+//  exact: eigenvectors of the Gram matrix X X^H (or X^H X);
+//  randomized (Halko-Martinsson-Tropp): Y = X Omega (k columns), q power
+//    iterations with re-orthonormalisation, Q = orth(Y), Rayleigh-Ritz on
+//    C = (Q^H X)(Q^H X)^H, W = Q * (top-r eigenvectors of C).  Used when
+//    k < n_side; otherwise the sketch spans the space and the exact path runs.
 template <typename R>
 nne_status subspace(nne_state* s, cx<R>* X, int rows, int cols, int r, int dir) {
   cudaStream_t st = s->ctx->stream;
   cx<R>* Hm = reinterpret_cast<cx<R>*>(s->H);
   cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
+  const cx<R> one = mk<R>(1, 0), zero = mk<R>(0, 0);
   const int n = dir > 0 ? rows : cols;
+  const int other = dir > 0 ? cols : rows;
+  const int k = s->omega_cols;
+  if (s->trunc == NNE_TRUNC_RSVD && s->d_omega && k < n && k >= r) {
+    cx<R>* Om = reinterpret_cast<cx<R>*>(s->d_omega);
+    cx<R>* Y = reinterpret_cast<cx<R>*>(s->rs_Y);    // n x k
+    cx<R>* Z = reinterpret_cast<cx<R>*>(s->rs_Z);    // other x k
+    cx<R>* Cm = reinterpret_cast<cx<R>*>(s->rs_C);   // k x k
+    cx<R>* Wk = reinterpret_cast<cx<R>*>(s->rs_W);   // k x r
+    const long long sY = s->rs_sY, sZ = s->rs_sZ, sC = s->rs_sC, sW = s->rs_sW;
+    // A = X (dir > 0) or X^H (dir < 0): A is n x other
+    const int opA = dir > 0 ? OP_N : OP_C, opAh = dir > 0 ? OP_C : OP_N;
+    CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Om, 0, k, zero, Y, sY, k, s->n_inst));
+    CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, s->qr_ws, s->n_inst));
+    for (int it = 0; it < s->power_iters; ++it) {
+      CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, s->n_inst));
+      CTRY(qr<R>(st, Z, sZ, other, k, Z, sZ, nullptr, 0, s->qr_ws, s->n_inst));
+      CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Z, sZ, k, zero, Y, sY, k, s->n_inst));
+      CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, s->qr_ws, s->n_inst));
+    }
+    if (k == r) {   // the sketch space itself is the answer
+      CTRY(copy_batched<R>(st, Y, sY, W, s->sU, (long long)n * k, s->n_inst));
+      CTRY(fix_columns<R>(st, W, s->sU, n, r, s->n_inst));
+      return NNE_OK;
+    }
+    // Bt = A^H Q (other x k); C = Bt^H Bt (k x k)
+    CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, s->n_inst));
+    CTRY(cgemm<R>(st, OP_C, OP_N, k, k, other, one, Z, sZ, k, Z, sZ, k, zero, Cm, sC, k, s->n_inst));
+    CTRY(eigh_top<R>(st, Cm, sC, k, r, Wk, sW, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
+    CTRY(cgemm<R>(st, OP_N, OP_N, n, r, k, one, Y, sY, k, Wk, sW, r, zero, W, s->sU, r, s->n_inst));
+    CTRY(fix_columns<R>(st, W, s->sU, n, r, s->n_inst));
+    return NNE_OK;
+  }
   if (dir > 0)
-    CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, cols, mk<R>(1, 0), X, s->sX, cols, X, s->sX, cols, mk<R>(0, 0), Hm,
-                  s->sH, rows, s->n_inst));
+    CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, cols, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, rows,
+                  s->n_inst));
   else
-    CTRY(cgemm<R>(st, OP_C, OP_N, cols, cols, rows, mk<R>(1, 0), X, s->sX, cols, X, s->sX, cols, mk<R>(0, 0), Hm,
-                  s->sH, cols, s->n_inst));
+    CTRY(cgemm<R>(st, OP_C, OP_N, cols, cols, rows, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, cols,
+                  s->n_inst));
   CTRY(eigh_top<R>(st, Hm, s->sH, n, r, W, s->sU, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
+  CTRY(fix_columns<R>(st, W, s->sU, n, r, s->n_inst));
   return NNE_OK;
 }
 
@@ -285,6 +353,7 @@ nne_status compress(nne_state* s, int chi_new) {
       CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, dr, mk<R>(1, 0), Xs, s->sX, dr, Xs, s->sX, dr, mk<R>(0, 0), Hm,
                     s->sH, rows, s->n_inst));
       CTRY(eigh_top<R>(st, Hm, s->sH, rows, r, W, s->sU, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
+      CTRY(fix_columns<R>(st, W, s->sU, rows, r, s->n_inst));
       CTRY(copy_batched<R>(st, W, s->sU, M, s->sstride[k], (long long)rows * r, s->n_inst));
       CTRY(cgemm<R>(st, OP_C, OP_N, r, dr, rows, mk<R>(1, 0), W, s->sU, r, Xs, s->sX, dr, mk<R>(0, 0), Cm, s->sR, dr,
                     s->n_inst));
@@ -310,6 +379,15 @@ nne_status read_err(nne_state* s) {
   if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
   if (h != 0) return set_error(h, "device-side failure status %d (non-finite or zero norm in a gate step)", h);
   return NNE_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 struct DeviceGuard {
@@ -354,13 +432,22 @@ nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_
                               void* G_out) {
   if (!ctx || n_gates < 0 || n_inst < 1 || !rates || (n_gates > 0 && (!U || !G_out)))
     return set_error(NNE_ERR_ARG, "nne_build_superops: bad arguments");
-  for (int i = 0; i < n_inst; ++i)
-    for (int c = 0; c < 4; ++c) {
-      const double p = rates[4 * i + c];
-      const double hi = c == 0 ? 16.0 / 15.0 : 1.0;
-      if (!(p >= 0.0 && p <= hi)) return set_error(NNE_ERR_ARG, "rate %d of instance %d out of range: %g", c, i, p);
-    }
   DeviceGuard g(ctx->device);
+  const bool u_dev = is_device_ptr(U), r_dev = is_device_ptr(rates);
+  if (!r_dev)
+    for (int i = 0; i < n_inst; ++i)
+      for (int c = 0; c < 4; ++c) {
+        const double p = rates[4 * i + c];
+        const double hi = c == 0 ? 16.0 / 15.0 : 1.0;
+        if (!(p >= 0.0 && p <= hi)) return set_error(NNE_ERR_ARG, "rate %d of instance %d out of range: %g", c, i, p);
+      }
+  if (u_dev && r_dev) {
+    // inputs already resident: no staging copies
+    ScratchF64& sc = scratch_snoise(ctx, n_inst);
+    if (!sc.p) return set_error(NNE_ERR_OOM, "superoperator scratch");
+    NNE_CUDA_TRY(build_superops(ctx->stream, n_gates, U, n_inst, rates, (double*)G_out, sc.p));
+    return NNE_OK;
+  }
   double *dU = nullptr, *dR = nullptr, *dS = nullptr;
   const size_t bu = sizeof(double) * 32 * (size_t)std::max(n_gates, 1), br = sizeof(double) * 4 * n_inst,
                bs = sizeof(double) * 512 * n_inst;
@@ -369,8 +456,8 @@ nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_
   NNE_CUDA_TRY(cudaMalloc(&dS, bs));
   nne_status rc = NNE_OK;
   cudaError_t e = cudaSuccess;
-  if (n_gates > 0) e = cudaMemcpyAsync(dU, U, sizeof(double) * 32 * n_gates, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dR, rates, br, cudaMemcpyHostToDevice, ctx->stream);
+  if (n_gates > 0) e = cudaMemcpyAsync(dU, U, sizeof(double) * 32 * n_gates, cudaMemcpyDefault, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dR, rates, br, cudaMemcpyDefault, ctx->stream);
   if (e == cudaSuccess) e = build_superops(ctx->stream, n_gates, dU, n_inst, dR, (double*)G_out, dS);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) rc = set_cuda_error(e, "build_superops", __FILE__, __LINE__);
@@ -479,6 +566,13 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
   if ((rc = s->mem.alloc(&s->eig_u8, (size_t)ew.u8_elems * n_inst)) != NNE_OK) return fail(rc);
   const QrWork qw = qr_workspace((int)N4, (int)N4);
   if ((rc = s->mem.alloc(&s->qr_ws, (size_t)qw.cx_elems * n_inst * s->esz)) != NNE_OK) return fail(rc);
+  s->bits.assign(n, 0);
+  if (init_bits)
+    for (int k = 0; k < n; ++k) s->bits[k] = init_bits[k] ? 1 : 0;
+  if ((rc = s->mem.alloc(&p, n)) != NNE_OK) return fail(rc);
+  s->d_bits = reinterpret_cast<uint8_t*>(p);
+  if (cudaMemcpy(s->d_bits, s->bits.data(), n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(set_error(NNE_ERR_CUDA, "cudaMemcpy bits"));
   // sweep buffers
   if ((rc = s->mem.alloc(&p, sizeof(int) * (n + 1))) != NNE_OK) return fail(rc);
   s->d_dims = reinterpret_cast<int*>(p);
@@ -511,8 +605,30 @@ void nne_destroy_state(nne_state* st) {
 }
 
 nne_status nne_set_sketch(nne_state* st, const void* omega, int rows, int cols, int power_iters) {
-  (void)st; (void)omega; (void)rows; (void)cols; (void)power_iters;
-  return set_error(NNE_ERR_UNIMPL, "randomized truncation not built yet");
+  if (!st || !omega || rows < 4 * st->dmax || cols < 1 || cols > 4 * st->dmax || power_iters < 0 || power_iters > 16)
+    return set_error(NNE_ERR_ARG, "nne_set_sketch: need rows >= 4*chi_max (%d), 1 <= cols <= 4*chi_max, 0 <= q <= 16",
+                     4 * st->dmax);
+  if (st->d_omega) return set_error(NNE_ERR_ARG, "nne_set_sketch: sketch already set");
+  DeviceGuard dg(st->ctx->device);
+  void* p = nullptr;
+  nne_status rc;
+  const size_t es = st->esz;
+  const long long N4 = 4LL * st->dmax;
+  if ((rc = st->mem.alloc(&p, (size_t)rows * cols * es)) != NNE_OK) return rc;
+  st->d_omega = p;
+  NNE_CUDA_TRY(cudaMemcpy(st->d_omega, omega, (size_t)rows * cols * es, cudaMemcpyHostToDevice));
+  st->rs_sY = N4 * cols;
+  st->rs_sZ = N4 * cols;
+  st->rs_sC = (long long)cols * cols;
+  st->rs_sW = (long long)cols * st->dmax;
+  if ((rc = st->mem.alloc(&st->rs_Y, (size_t)st->rs_sY * st->n_inst * es)) != NNE_OK) return rc;
+  if ((rc = st->mem.alloc(&st->rs_Z, (size_t)st->rs_sZ * st->n_inst * es)) != NNE_OK) return rc;
+  if ((rc = st->mem.alloc(&st->rs_C, (size_t)st->rs_sC * st->n_inst * es)) != NNE_OK) return rc;
+  if ((rc = st->mem.alloc(&st->rs_W, (size_t)st->rs_sW * st->n_inst * es)) != NNE_OK) return rc;
+  st->omega_rows = rows;
+  st->omega_cols = cols;
+  st->power_iters = power_iters;
+  return NNE_OK;
 }
 
 nne_status nne_apply_layer(nne_state* st, int n_gates, const int* left_qubit, const void* G, int direction) {
@@ -641,6 +757,25 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
   cudaFree(dout);
   cudaFree(dst);
   return rc;
+}
+
+nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits) {
+  if (!st) return set_error(NNE_ERR_ARG, "null state");
+  DeviceGuard dg(st->ctx->device);
+  cudaStream_t s = st->ctx->stream;
+  if (init_bits) {
+    for (int k = 0; k < st->n; ++k) st->bits[k] = init_bits[k] ? 1 : 0;
+    NNE_CUDA_TRY(cudaMemcpyAsync(st->d_bits, st->bits.data(), st->n, cudaMemcpyHostToDevice, s));
+  }
+  cudaError_t e = st->dtype == NNE_C64
+                      ? product_state<float>(s, st->n, (void* const*)st->d_site, st->d_stride, st->n_inst, st->d_bits)
+                      : product_state<double>(s, st->n, (void* const*)st->d_site, st->d_stride, st->n_inst, st->d_bits);
+  if (e != cudaSuccess) return set_cuda_error(e, "product_state", __FILE__, __LINE__);
+  NNE_CUDA_TRY(cudaMemsetAsync(st->d_lognorm, 0, sizeof(double) * 2 * st->n_inst, s));
+  NNE_CUDA_TRY(cudaMemsetAsync(st->d_err, 0, sizeof(int), s));
+  std::fill(st->dims.begin(), st->dims.end(), 1);
+  st->centre = 0;
+  return NNE_OK;
 }
 
 nne_status nne_sync(nne_state* st) {

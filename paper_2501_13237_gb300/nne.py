@@ -28,7 +28,7 @@ SYMBOLS = (
     "nne_ctx_create", "nne_ctx_destroy", "nne_ctx_bytes_in_use", "nne_last_error", "nne_build_superops",
     "nne_create_state", "nne_destroy_state", "nne_set_sketch", "nne_apply_layer", "nne_truncate", "nne_expect",
     "nne_extrapolate", "nne_sync", "nne_state_info", "nne_state_read_site", "nne_state_write_site",
-    "nne_state_set_centre",
+    "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
 )
 
 
@@ -70,6 +70,10 @@ def load(path: str = LIB_PATH):
         "nne_state_read_site": (i32, [vp, i32, i32, vp, sz]),
         "nne_state_write_site": (i32, [vp, i32, i32, i32, i32, vp]),
         "nne_state_set_centre": (i32, [vp, i32]),
+        "nne_reset_state": (i32, [vp, vp]),
+        "nne_kernel_launches": (C.c_longlong, []),
+        "nne_prof_enable": (None, [i32]),
+        "nne_prof_collect": (i32, [vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -118,14 +122,24 @@ class Context:
     def bytes_in_use(self) -> int:
         return int(load().nne_ctx_bytes_in_use(self.h))
 
-    def build_superops(self, U: np.ndarray, rates: np.ndarray):
-        """a1: U (g,4,4) complex128, rates (n_inst,4) -> device tensor (n_inst, g, 16, 16) complex128."""
+    def build_superops(self, U, rates, out=None):
+        """a1: U (g,4,4) complex128, rates (n_inst,4) float64 -- numpy (host) or torch CUDA
+        tensors (device) -> device tensor (n_inst, g, 16, 16) complex128."""
         import torch
-        U = np.ascontiguousarray(U, dtype=np.complex128)
-        rates = np.ascontiguousarray(rates, dtype=np.float64).reshape(-1, 4)
-        g, ni = U.shape[0], rates.shape[0]
-        G = torch.empty((ni, g, 16, 16), dtype=torch.complex128, device=f"cuda:{self.device}")
-        _check(load().nne_build_superops(self.h, g, _hptr(U), ni, _hptr(rates), C.c_void_p(_dptr(G))))
+
+        def ptr(a, dt):
+            if isinstance(a, torch.Tensor):
+                assert a.is_cuda and a.is_contiguous() and a.dtype == dt
+                return C.c_void_p(_dptr(a)), a.shape
+            a = np.ascontiguousarray(a, dtype=np.complex128 if dt == torch.complex128 else np.float64)
+            return _hptr(a), a.shape, a
+        pu = ptr(U, torch.complex128)
+        pr = ptr(rates, torch.float64)
+        g = pu[1][0]
+        ni = (pr[1][0] * pr[1][1]) // 4 if len(pr[1]) == 2 else pr[1][0] // 4
+        G = out if out is not None else torch.empty((ni, g, 16, 16), dtype=torch.complex128,
+                                                    device=f"cuda:{self.device}")
+        _check(load().nne_build_superops(self.h, g, pu[0], ni, pr[0], C.c_void_p(_dptr(G))))
         return G
 
     def extrapolate(self, lambdas, values, log_fid=None, method=FIT_EXP_LOGLIN, degree=2, lambda_star=1.0,
@@ -215,3 +229,28 @@ class State:
 
     def set_centre(self, c: int):
         _check(load().nne_state_set_centre(self.h, c))
+
+    def reset(self, bits=None):
+        b = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)
+        _check(load().nne_reset_state(self.h, _hptr(b)))
+
+
+PROF_CLASSES = ("gemm", "superop_epilogue", "tridiag", "bisect", "inviter", "backtransform", "qr_factor",
+                "qr_formq", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit")
+
+
+def kernel_launches() -> int:
+    return int(load().nne_kernel_launches())
+
+
+def prof_enable(on: bool):
+    load().nne_prof_enable(1 if on else 0)
+
+
+def prof_collect():
+    """{class: (total_ms, launches, work)} since the last collect (synchronises)."""
+    ms = np.zeros(16)
+    cnt = np.zeros(16, np.int64)
+    wk = np.zeros(16)
+    load().nne_prof_collect(_hptr(ms), _hptr(cnt), _hptr(wk), 16)
+    return {name: (float(ms[i]), int(cnt[i]), float(wk[i])) for i, name in enumerate(PROF_CLASSES)}

@@ -35,20 +35,30 @@ def test_superops_match_oracle(ctx):
 
 
 @pytest.mark.parametrize("dtype", [1, 0])
-@pytest.mark.parametrize("dl,dm,dr,chi,direction", [
-    (24, 40, 20, 50, +1), (24, 40, 20, 50, -1),      # truncating, ragged shapes
-    (3, 9, 5, 64, +1), (3, 9, 5, 64, -1),            # r = 4 dl or 4 dr: identity branch
-    (16, 64, 16, 64, +1), (7, 33, 30, 37, -1),       # several tiles, odd tails
+@pytest.mark.parametrize("dl,dm,dr,chi,direction,sk", [
+    (24, 40, 20, 50, +1, 0), (24, 40, 20, 50, -1, 0),      # truncating, ragged shapes
+    (3, 9, 5, 64, +1, 0), (3, 9, 5, 64, -1, 0),            # r = 4 dl or 4 dr: identity branch
+    (16, 64, 16, 64, +1, 0), (7, 33, 30, 37, -1, 0),       # several tiles, odd tails
+    (170, 100, 60, 200, +1, 0),                            # Gram above the shared-memory size
+    (24, 24, 20, 24, +1, 28), (24, 24, 20, 24, -1, 28),    # randomized range finder, k = 28
+    (60, 64, 50, 64, +1, 100), (60, 64, 50, 64, -1, 72),
 ])
-def test_single_gate_step(ctx, dtype, dl, dm, dr, chi, direction):
-    """One gate step on sites (3, 4) of an 8-site chain (capacities
-    min(chi, 4^k, 4^(8-k)) admit the shapes) vs the oracle's two-site update."""
+def test_single_gate_step(ctx, dtype, dl, dm, dr, chi, direction, sk):
+    """One gate step on sites (4, 5) of a 10-site chain (capacities
+    min(chi, 4^k, 4^(10-k)) admit the shapes) vs the oracle's two-site update
+    (exact SVD, or the randomized range finder with the same sketch, q = 1)."""
     from paper_2501_13237_gb300 import nne
-    rng = np.random.default_rng(dl * 1000 + dr + (direction > 0))
+    rng = np.random.default_rng(dl * 1000 + dr + (direction > 0) + sk)
     A = rand_c(rng, (dl, 4, dm))
     B = rand_c(rng, (dm, 4, dr))
-    n, q = 8, 3
-    st = nne.State(ctx, n, chi, 2, dtype)
+    n, q = 10, 4
+    st = nne.State(ctx, n, chi, 2, dtype, nne.TRUNC_RSVD if sk else nne.TRUNC_EXACT)
+    sketch = None
+    if sk:
+        rows = 4 * min(chi, 256)
+        om = wl.gaussian_sketch(rows, sk, 5).astype(np.complex64 if dtype == 0 else np.complex128)
+        st.set_sketch(om, 1)
+        sketch = om.astype(np.complex128)
     for inst in range(2):
         st.write_site(inst, q, A)
         st.write_site(inst, q + 1, B)
@@ -62,7 +72,7 @@ def test_single_gate_step(ctx, dtype, dl, dm, dr, chi, direction):
     Gh = G.cpu().numpy()
     tol = TOL[dtype]
     for inst in range(2):
-        left, right, f, nrm, s = mps.two_site_update(A, B, Gh[inst, 0], chi, direction)
+        left, right, f, nrm, s = mps.two_site_update(A, B, Gh[inst, 0], chi, direction, sketch, 1)
         L = st.read_site(inst, q).astype(np.complex128)
         R = st.read_site(inst, q + 1).astype(np.complex128)
         got = np.einsum("asc,ctb->astb", L, R).reshape(4 * dl, 4 * dr)
@@ -129,6 +139,29 @@ def test_truncated_vs_oracle_mps(ctx, dtype, tol, n, depth, chi, seed):
         assert np.abs(vals[i] - ref).max() < tol, (i, np.abs(vals[i] - ref).max())
         assert abs(lf[i] - ref_st.log_fid) < tol * max(1.0, abs(ref_st.log_fid))
         assert ref_st.log_fid < -1e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 1e-4)])
+def test_truncated_rsvd_vs_oracle_mps(ctx, dtype, tol):
+    from paper_2501_13237_gb300 import nne, runner
+    n, chi, k = 10, 16, 24
+    c = wl.brickwork_circuit(n, 10, 5)
+    noise = wl.NoiseModel(depol2=0.02, amp_damp=0.01, dephase=0.01)
+    rates = np.stack([noise.rates(l) for l in (1.0, 3.0)])
+    paulis = wl.pauli_codes(wl.obs_z(n) + wl.obs_xx(n), n)
+    om = wl.gaussian_sketch(4 * chi, k, 9).astype(np.complex64 if dtype == 0 else np.complex128)
+    # one power iteration: with two, the range finder itself is chaotic on this
+    # workload (a 1e-13 change of the sketch moves <Z> by 1e-2 in the oracle)
+    st = nne.State(ctx, n, chi, 2, dtype, nne.TRUNC_RSVD)
+    st.set_sketch(om, 1)
+    runner.evolve(st, runner.build_layer_superops(ctx, c, rates))
+    vals, lf = st.expect(paulis)
+    for i in range(2):
+        ref_st = mps.run(c, rates[i], chi, sketch=om.astype(np.complex128), power_iters=1)
+        ref = ref_st.expect_codes(paulis)
+        assert np.abs(vals[i] - ref).max() < tol, np.abs(vals[i] - ref).max()
+        assert abs(lf[i] - ref_st.log_fid) < tol * max(1.0, abs(ref_st.log_fid))
+    st.close()
 
 
 @pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 1e-4)])
