@@ -18,7 +18,10 @@ DESIGN.md).  Each subcircuit (Sec. 2.1.2 "Approximate emulation"):
   4. X = theta' as a (4 chi_l) x (4 chi_r) matrix, SVD X = U S V^dagger, keep
      r = min(chi, 4 chi_l, 4 chi_r) singular triplets (no relative cutoff):
      by Eckart-Young this is the closest bond-chi state to C_l rho~_{l-1}
-     when the rest of the chain is in canonical form;
+     when the rest of the chain is in canonical form.  When nothing is cut
+     (r = min(4 chi_l, 4 chi_r)) the split is exact and any basis will do:
+     the identity when the isometry's side has dimension r, else the Q of a
+     QR factorisation;
   5. normalise the kept part to Frobenius norm 1 (the "closest ... state with
      Frobenius norm 1"), accumulating the dropped scale in log_norm;
   6. partial fidelity f_l = sum_{i<=r} s_i^2 / sum_i s_i^2, which is the
@@ -251,6 +254,16 @@ def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direc
         if direction > 0:
             return np.eye(4 * cl, dtype=X.dtype).reshape(cl, 4, r), (X / nrm).reshape(r, 4, cr), 1.0, nrm, S
         return (X / nrm).reshape(cl, 4, r), np.eye(4 * cr, dtype=X.dtype).reshape(r, 4, cr), 1.0, nrm, S
+    if r == min(4 * cl, 4 * cr):
+        # nothing is cut, but the isometry's side is the larger one: exact QR split
+        S = np.linalg.svd(X, compute_uv=False)
+        if direction > 0:
+            Q, Rm = qr_fixed(X)
+            nrm = float(np.linalg.norm(Rm))
+            return Q.reshape(cl, 4, r), (Rm / nrm).reshape(r, 4, cr), 1.0, nrm, S
+        Q, Rm = qr_fixed(X.conj().T)
+        nrm = float(np.linalg.norm(Rm))
+        return (Rm.conj().T / nrm).reshape(cl, 4, r), Q.conj().T.reshape(r, 4, cr), 1.0, nrm, S
     if sketch is not None:
         S = np.linalg.svd(X, compute_uv=False)
         total = float(np.sum(np.abs(X) ** 2))

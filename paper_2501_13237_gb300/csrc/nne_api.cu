@@ -304,6 +304,13 @@ nne_status gate_step(nne_state* s, int q, const double* G, long long sG, int dir
       CTRY(identity<R>(st, A, s->sstride[q], rows, r, s->n_inst));
       CTRY(copy_batched<R>(st, X, s->sX, B, s->sstride[q + 1], countX, s->n_inst));
       TRY(finish_split<R>(s, B, s->sstride[q + 1], countX, nullptr, 0, 0));
+    } else if (r == cols) {
+      // nothing is cut: X = Q R exactly (Householder), left factor Q, centre R
+      cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
+      CTRY(qr<R>(st, X, s->sX, rows, cols, Q, s->sT, B, s->sstride[q + 1], s->qr_ws, s->n_inst));
+      CTRY(fix_qr<R>(st, Q, s->sT, rows, r, B, s->sstride[q + 1], cols, s->n_inst));
+      CTRY(copy_batched<R>(st, Q, s->sT, A, s->sstride[q], (long long)rows * r, s->n_inst));
+      TRY(finish_split<R>(s, B, s->sstride[q + 1], (long long)r * cols, nullptr, 0, 0));
     } else {
       TRY(subspace<R>(s, X, rows, cols, r, +1));
       cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
@@ -319,6 +326,17 @@ nne_status gate_step(nne_state* s, int q, const double* G, long long sG, int dir
       CTRY(identity<R>(st, B, s->sstride[q + 1], r, cols, s->n_inst));
       CTRY(copy_batched<R>(st, X, s->sX, A, s->sstride[q], countX, s->n_inst));
       TRY(finish_split<R>(s, A, s->sstride[q], countX, nullptr, 0, 0));
+    } else if (r == rows) {
+      // nothing is cut: X^H = Q R exactly, right factor Q^H, centre R^H
+      cx<R>* Xh = reinterpret_cast<cx<R>*>(s->H);
+      cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
+      cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
+      CTRY(transpose<R>(st, true, X, s->sX, rows, cols, cols, Xh, s->sH, rows, s->n_inst));
+      CTRY(qr<R>(st, Xh, s->sH, cols, rows, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));
+      CTRY(fix_qr<R>(st, Q, s->sT, cols, r, Rr, s->sR, rows, s->n_inst));
+      CTRY(transpose<R>(st, true, Q, s->sT, cols, r, r, B, s->sstride[q + 1], cols, s->n_inst));
+      CTRY(transpose<R>(st, true, Rr, s->sR, r, rows, rows, A, s->sstride[q], r, s->n_inst));
+      TRY(finish_split<R>(s, A, s->sstride[q], (long long)rows * r, nullptr, 0, 0));
     } else {
       TRY(subspace<R>(s, X, rows, cols, r, -1));
       cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
