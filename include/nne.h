@@ -169,6 +169,24 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
  * or NULL for the bits given at creation.  Enqueued on the context stream. */
 nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits);
 
+/* The fit of nne_extrapolate for callers that cannot allocate device memory
+ * when they ask for it (no counterpart in the paper): a request loop whose HBM
+ * budget is already committed to resident states, where a new cudaMalloc can
+ * fail, or latency-critical code that cannot pay for cudaMalloc/cudaFree, which
+ * may synchronise the device.  Same arguments, results and kernel as
+ * nne_extrapolate, but the device-side copies of the inputs and outputs live
+ * in one fixed array of about 0.55 MB compiled into the library (present on
+ * every GPU that loads it until the process exits); nothing is allocated.
+ * Limits: n_lambda <= 64 and n_obs <= 1024, larger sizes return NNE_ERR_ARG.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU race; calls made one after
+ * another are safe (each call waits for its results before returning). */
+nne_status nne_extrapolate_noalloc(nne_ctx* ctx, int n_lambda, const double* lambdas, const double* values,
+                                   const double* log_fid, int n_obs, int method, int degree,
+                                   double lambda_star, const double* y_zero, double* out,
+                                   int32_t* per_obs_status);
+
 /* Wait for the state's enqueued work; returns the first device-side error. */
 nne_status nne_sync(nne_state* st);
 

@@ -97,4 +97,7 @@ cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, 
                             const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
                             const double* d_yzero, double* d_out, int* d_status);
 
+// Device ordinal and stream of a context (defined with the context in nne_api.cu).
+void ctx_device_stream(const nne_ctx* ctx, int* device, cudaStream_t* stream);
+
 }  // namespace nne

@@ -50,6 +50,13 @@ struct nne_ctx {
   }
 };
 
+namespace nne {
+void ctx_device_stream(const nne_ctx* ctx, int* device, cudaStream_t* stream) {
+  *device = ctx->device;
+  *stream = ctx->stream;
+}
+}  // namespace nne
+
 namespace {
 
 struct DevAlloc {

@@ -29,6 +29,7 @@ SYMBOLS = (
     "nne_create_state", "nne_destroy_state", "nne_set_sketch", "nne_apply_layer", "nne_truncate", "nne_expect",
     "nne_extrapolate", "nne_sync", "nne_state_info", "nne_state_read_site", "nne_state_write_site",
     "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
+    "nne_extrapolate_noalloc",
 )
 
 
@@ -74,6 +75,7 @@ def load(path: str = LIB_PATH):
         "nne_kernel_launches": (C.c_longlong, []),
         "nne_prof_enable": (None, [i32]),
         "nne_prof_collect": (i32, [vp, vp, vp, i32]),
+        "nne_extrapolate_noalloc": (i32, [vp, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -156,6 +158,24 @@ class Context:
         st = np.zeros(no, np.int32)
         _check(load().nne_extrapolate(self.h, nl, _hptr(lam), _hptr(vals), _hptr(lf), no, method, degree,
                                       float(lambda_star), _hptr(yz), _hptr(out), _hptr(st)))
+        return out, st
+
+
+    def extrapolate_noalloc(self, lambdas, values, log_fid=None, method=FIT_EXP_LOGLIN, degree=2,
+                            lambda_star=1.0, y_zero=None):
+        """nne_extrapolate_noalloc: the same fit staged through the library's fixed device array
+        (for callers that cannot allocate device memory at call time)."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        vals = np.ascontiguousarray(values, dtype=np.float64)
+        if vals.ndim == 1:
+            vals = vals[:, None]
+        nl, no = vals.shape
+        lf = None if log_fid is None else np.ascontiguousarray(log_fid, dtype=np.float64)
+        yz = None if y_zero is None else np.ascontiguousarray(y_zero, dtype=np.float64)
+        out = np.zeros(no)
+        st = np.zeros(no, np.int32)
+        _check(load().nne_extrapolate_noalloc(self.h, nl, _hptr(lam), _hptr(vals), _hptr(lf), no, method, degree,
+                                              float(lambda_star), _hptr(yz), _hptr(out), _hptr(st)))
         return out, st
 
 
