@@ -62,9 +62,10 @@ typedef enum { NNE_C64 = 0, NNE_C128 = 1 } nne_dtype;
 /* Truncation algorithm of a gate step.
  * NNE_TRUNC_EXACT: eigenvectors of the full (4 chi_l)^2 Gram matrix X X^dagger
  *   (or X^dagger X), i.e. the exact best rank-chi approximation (Eckart-Young).
- * NNE_TRUNC_RSVD: randomized range finder with q power iterations and a
- *   Rayleigh-Ritz step on a (chi + p)-dimensional sketch (Halko, Martinsson &
- *   Tropp 2011); the sketch matrix is an input (nne_set_sketch).  Equals
+ * NNE_TRUNC_RSVD: randomized range finder with q power iterations
+ *   (Q <- orth(X X^H Q)) and a Rayleigh-Ritz step on a (chi + p)-dimensional
+ *   sketch (Halko, Martinsson & Tropp 2011); the sketch matrix is an input
+ *   (nne_set_sketch).  Equals
  *   NNE_TRUNC_EXACT whenever chi + p covers the rank bound of the gate. */
 typedef enum { NNE_TRUNC_EXACT = 0, NNE_TRUNC_RSVD = 1 } nne_trunc;
 
@@ -186,6 +187,20 @@ nne_status nne_extrapolate_noalloc(nne_ctx* ctx, int n_lambda, const double* lam
                                    const double* log_fid, int n_obs, int method, int degree,
                                    double lambda_star, const double* y_zero, double* out,
                                    int32_t* per_obs_status);
+
+/* Batched complex64 GEMM, C[z] = alpha op(A[z]) op(B[z]) + beta C[z] (row-major,
+ * op 0 = N, 1 = conjugate transpose; matrix z at pointer + z * stride elements),
+ * the same routine every gate step uses: tcgen05 tensor cores with split-TF32
+ * products for large shapes, float32 SIMT otherwise.  Device pointers;
+ * alpha/beta host (re, im).  Synchronises the context stream. */
+nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, const float* alpha, const void* A,
+                         int lda, long long stride_a, const void* B, int ldb, long long stride_b,
+                         const float* beta, void* C, int ldc, long long stride_c, int batch);
+
+/* Library options: NNE_OPT_TENSOR_CORES (default 1) selects the tcgen05 path of
+ * complex64 GEMMs (0 = float32 SIMT everywhere, for comparisons). */
+#define NNE_OPT_TENSOR_CORES 0
+void nne_set_option(int option, int value);
 
 /* Wait for the state's enqueued work; returns the first device-side error. */
 nne_status nne_sync(nne_state* st);

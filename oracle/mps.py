@@ -218,7 +218,7 @@ def theta_superop(A: np.ndarray, B: np.ndarray, G: np.ndarray) -> np.ndarray:
 
 def range_finder_isometry(A: np.ndarray, r: int, omega: np.ndarray, q: int) -> np.ndarray:
     """Top-r left singular subspace of A (n x m) by the randomized range finder:
-    Y = A Omega (k columns), q power iterations A (A^H Q) with re-orthonormalisation,
+    Y = A Omega (k columns), q power iterations Q <- orth(A (A^H Q)),
     Rayleigh-Ritz on C = (Q^H A)(Q^H A)^H, W = Q * (top-r eigenvectors of C)
     (Halko, Martinsson & Tropp 2011, Algs. 4.4 and 5.1).  When k >= n the sketch
     spans the whole space and the exact top-r eigenvectors of A A^H are returned."""
@@ -229,8 +229,7 @@ def range_finder_isometry(A: np.ndarray, r: int, omega: np.ndarray, q: int) -> n
         return fix_columns(V[:, ::-1][:, :r])
     Q, _ = np.linalg.qr(A @ omega[:m, :k])
     for _ in range(q):
-        Z, _ = np.linalg.qr(A.conj().T @ Q)
-        Q, _ = np.linalg.qr(A @ Z)
+        Q, _ = np.linalg.qr(A @ (A.conj().T @ Q))
     Bm = Q.conj().T @ A
     ev, V = np.linalg.eigh(Bm @ Bm.conj().T)
     return fix_columns(Q @ V[:, ::-1][:, :r])

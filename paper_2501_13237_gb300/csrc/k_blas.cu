@@ -1,5 +1,7 @@
 // Batched complex GEMM (SIMT), the superoperator epilogue, and small
 // elementwise / reduction kernels used by the gate step.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace nne {
@@ -79,6 +81,10 @@ cudaError_t cgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<R> 
                   long long sA, int lda, const cx<R>* B, long long sB, int ldb, cx<R> beta, cx<R>* C,
                   long long sC, int ldc, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (std::is_same<R, float>::value && tensor_cores_enabled() && M >= 64 && N >= 64 && K >= 64)
+    return cgemm_tc(st, opA, opB, M, N, K, *reinterpret_cast<const cx<float>*>(&alpha),
+                    reinterpret_cast<const cx<float>*>(A), sA, lda, reinterpret_cast<const cx<float>*>(B), sB, ldb,
+                    *reinterpret_cast<const cx<float>*>(&beta), reinterpret_cast<cx<float>*>(C), sC, ldc, batch);
   ProfScope ps(st, K_GEMM, 1, 8.0 * M * N * (double)K * batch);
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   if (opA == OP_N && opB == OP_N)

@@ -37,11 +37,12 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
   cx<R>* e = eb + (long long)z * ldde;
   cx<R>* Vh = Vhb + z * sVh;
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* Hl = reinterpret_cast<cx<R>*>(smem_raw);     // [maxloc][n]
-  cx<R>* v = Hl + (long long)maxloc * n;
-  cx<R>* w = v + n;
+  cx<R>* Hl = reinterpret_cast<cx<R>*>(smem_raw);     // [maxloc][n] own rows
+  cx<R>* vbuf = Hl + (long long)maxloc * n;           // 2 x n: column j (pushed by its owner), double-buffered
+  cx<R>* w = vbuf + 2 * n;
   cx<R>* p = w + n;
-  __shared__ double ks[2];
+  __shared__ double ks[2][16];                        // K partials pushed by every CTA
+  __shared__ R dpush[2];                              // diagonal entry pushed with the column
   __shared__ double red[32];
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
   const int nloc = n > rank ? (n - rank + CS - 1) / CS : 0;
@@ -49,12 +50,19 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
     const int li = (int)(e2 / n), c = (int)(e2 % n);
     Hl[e2] = H[(long long)(rank + li * CS) * n + c];
   }
+  // column 0 below the diagonal = conj(row 0 tail), pushed by the owner of row 0
+  if (rank == 0) {
+    for (int t = tid; t + 1 < n; t += nth) {
+      const cx<R> x = conj(Hl[1 + t]);
+      for (int c = 0; c < CS; ++c) *cluster.map_shared_rank(vbuf + t, c) = x;
+    }
+    if (tid < CS) *cluster.map_shared_rank(&dpush[0], tid) = Hl[0].re;
+  }
   cluster.sync();
   for (int j = 0; j + 2 < n; ++j) {
-    const int m = n - j - 1, owner = j % CS, lo = j / CS, buf = j & 1;
-    const cx<R>* rowj = cluster.map_shared_rank(Hl + (long long)lo * n, owner);
-    for (int t = tid; t < m; t += nth) v[t] = conj(rowj[j + 1 + t]);
-    const R djj = rowj[j].re;
+    const int m = n - j - 1, owner = j % CS, buf = j & 1;
+    cx<R>* v = vbuf + buf * n;
+    const R djj = dpush[buf];
     // Householder vector (every CTA, same arithmetic)
     double s = 0;
     for (int t = tid; t < m; t += nth) s += (double)norm2(v[t]);
@@ -87,17 +95,25 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
     for (int li = lstart + warp; li < nloc; li += nw) {
       const int i = rank + li * CS, t = i - j - 1;
       const cx<R>* row = Hl + (long long)li * n + (j + 1);
-      cx<R> acc = mk<R>(0, 0);
-      for (int k = lane; k < m; k += 32) fma_(acc, row[k], v[k]);
+      cx<R> a0 = mk<R>(0, 0), a1 = a0, a2 = a0, a3 = a0;
+      int k = lane;
+      for (; k + 96 < m; k += 128) {
+        fma_(a0, row[k], v[k]);
+        fma_(a1, row[k + 32], v[k + 32]);
+        fma_(a2, row[k + 64], v[k + 64]);
+        fma_(a3, row[k + 96], v[k + 96]);
+      }
+      for (; k < m; k += 32) fma_(a0, row[k], v[k]);
+      cx<R> acc = (a0 + a1) + (a2 + a3);
       acc = warp_sum(acc);
       if (lane < CS) *cluster.map_shared_rank(p + t, lane) = acc;
       if (lane == 0) kp += (double)v[t].re * acc.re + (double)v[t].im * acc.im;
     }
     kp = bsum(kp, red);
-    if (tid == 0) ks[buf] = kp;
+    if (tid < CS) *cluster.map_shared_rank(&ks[buf][rank], tid) = kp;
     cluster.sync();
     double K = 0;
-    for (int c = 0; c < CS; ++c) K += *cluster.map_shared_rank(&ks[buf], c);
+    for (int c = 0; c < CS; ++c) K += ks[buf][c];
     const R twoK = (R)(2.0 * K);
     for (int t = tid; t < m; t += nth) w[t] = mk<R>(2 * p[t].re - twoK * v[t].re, 2 * p[t].im - twoK * v[t].im);
     __syncthreads();
@@ -105,6 +121,7 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
       const int i = rank + li * CS, t = i - j - 1;
       cx<R>* row = Hl + (long long)li * n + (j + 1);
       const cx<R> vt = v[t], wt = w[t];
+#pragma unroll 4
       for (int k = lane; k < m; k += 32) {
         cx<R> a = row[k];
         const cx<R> wk = w[k], vk = v[k];
@@ -112,6 +129,17 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
         a.im -= vt.im * wk.re - vt.re * wk.im + wt.im * vk.re - wt.re * vk.im;
         row[k] = a;
       }
+    }
+    // the owner of row j+1 pushes its updated tail (the next column) and diagonal
+    if (j + 3 < n && rank == (j + 1) % CS) {
+      __syncthreads();
+      const cx<R>* rn = Hl + (long long)((j + 1) / CS) * n;
+      cx<R>* vn = vbuf + (buf ^ 1) * n;
+      for (int t = tid; t + j + 2 < n; t += nth) {
+        const cx<R> x = conj(rn[j + 2 + t]);
+        for (int c = 0; c < CS; ++c) *cluster.map_shared_rank(vn + t, c) = x;
+      }
+      if (tid < CS) *cluster.map_shared_rank(&dpush[buf ^ 1], tid) = rn[j + 1].re;
     }
     cluster.sync();
   }
@@ -215,7 +243,7 @@ template <typename R>
 int smem_cluster_size(int n) {
   for (int cs = 1; cs <= 16; cs *= 2) {
     const size_t maxloc = (n + cs - 1) / cs;
-    const size_t bytes = sizeof(cx<R>) * (maxloc * n + 3 * (size_t)n);
+    const size_t bytes = sizeof(cx<R>) * (maxloc * n + 4 * (size_t)n);
     if (bytes <= SMEM_LIMIT && (cs >= 16 || maxloc <= 64)) return cs;
   }
   return 0;
@@ -227,7 +255,7 @@ cudaError_t tridiag_smem(cudaStream_t st, const cx<R>* H, long long sH, int n, R
   const int cs = smem_cluster_size<R>(n);
   if (cs == 0) return cudaErrorInvalidValue;
   const int maxloc = (n + cs - 1) / cs;
-  const size_t smem = sizeof(cx<R>) * ((size_t)maxloc * n + 3 * (size_t)n);
+  const size_t smem = sizeof(cx<R>) * ((size_t)maxloc * n + 4 * (size_t)n);
   ProfScope ps(st, K_TRIDIAG);
   return launch_cl(tridiag_smem_kernel<R>, cs, batch, smem, st, H, sH, n, d, e, ldde, Vh, sVh, maxloc);
 }

@@ -14,6 +14,7 @@ namespace cg = cooperative_groups;
 namespace nne {
 
 constexpr int QB = 32;   // panel width
+constexpr int PS = QB + 1;   // padded row stride of the shared-memory panel (avoids bank conflicts)
 
 template <typename R>
 __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, int lda, int m, int pb, int bw,
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
   cx<R>* V = Vb + z * sV;
   cx<R>* T = Tb + z * sT;
   extern __shared__ unsigned char smem_raw[];
-  cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);       // [maxloc][QB]
+  cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);       // [maxloc][PS]
   __shared__ double pn[2];
   __shared__ cx<R> x0s[2];
   __shared__ cx<R> pw[2][QB];
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
   for (int e = tid; e < nloc * QB; e += blockDim.x) {
     const int li = e / QB, c = e % QB;
     const long long gi = pb + rank + (long long)li * CS;
-    P[li * QB + c] = c < bw ? A[gi * lda + pb + c] : mk<R>(0, 0);
+    P[li * PS + c] = c < bw ? A[gi * lda + pb + c] : mk<R>(0, 0);
   }
   __syncthreads();
   for (int j = 0; j < bw; ++j) {
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
     // first local row with panel index >= j
     const int lstart = (j - rank + CS - 1) / CS > 0 ? (j - rank + CS - 1) / CS : 0;
     double s = 0;
-    for (int li = lstart + tid; li < nloc; li += blockDim.x) s += (double)norm2(P[li * QB + j]);
+    for (int li = lstart + tid; li < nloc; li += blockDim.x) s += (double)norm2(P[li * PS + j]);
     s = warp_sum_r(s);
     if (lane == 0) dred[grp] = s;
     __syncthreads();
@@ -61,12 +62,20 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
       double t = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += dred[w];
       pn[buf] = t;
-      if (rank == owner) x0s[buf] = P[ljo * QB + j];
+      if (rank == owner) x0s[buf] = P[ljo * PS + j];
     }
     cluster.sync();
-    double xn2 = 0;
-    for (int c = 0; c < CS; ++c) xn2 += *cluster.map_shared_rank(&pn[buf], c);
-    const cx<R> x0 = *cluster.map_shared_rank(&x0s[buf], owner);
+    __shared__ double xn2s;
+    __shared__ cx<R> x0l;
+    if (tid == 0) {
+      double t2 = 0;
+      for (int c = 0; c < CS; ++c) t2 += *cluster.map_shared_rank(&pn[buf], c);
+      xn2s = t2;
+      x0l = *cluster.map_shared_rank(&x0s[buf], owner);
+    }
+    __syncthreads();
+    const double xn2 = xn2s;
+    const cx<R> x0 = x0l;
     const double ax0 = sqrt((double)norm2(x0)), xn = sqrt(xn2);
     cx<R> alpha = mk<R>(0, 0);
     double un = 0;
@@ -82,9 +91,9 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
     }
     // v = (x - alpha e_0) / un on own rows
     for (int li = lstart + tid; li < nloc; li += blockDim.x) {
-      cx<R> u = P[li * QB + j];
+      cx<R> u = P[li * PS + j];
       if (rank == owner && li == ljo) u = u - alpha;
-      P[li * QB + j] = inv * u;
+      P[li * PS + j] = inv * u;
     }
     __syncthreads();
     // partial w_c = sum conj(v_i) P[i][c], c in (j, bw)
@@ -92,7 +101,7 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
       const int c = lane;
       cx<R> acc = mk<R>(0, 0);
       if (c > j && c < bw)
-        for (int li = lstart + grp; li < nloc; li += 8) fmac_(acc, P[li * QB + j], P[li * QB + c]);
+        for (int li = lstart + grp; li < nloc; li += 8) fmac_(acc, P[li * PS + j], P[li * PS + c]);
       red[grp][c] = acc;
     }
     __syncthreads();
@@ -114,8 +123,8 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
       for (int e = tid; e < (nloc - lstart) * QB; e += blockDim.x) {
         const int li = lstart + e / QB, c = e % QB;
         if (c > j && c < bw) {
-          const cx<R> vi = P[li * QB + j];
-          P[li * QB + c] = P[li * QB + c] - vi * wfull[c];
+          const cx<R> vi = P[li * PS + j];
+          P[li * PS + c] = P[li * PS + c] - vi * wfull[c];
         }
       }
       __syncthreads();
@@ -128,7 +137,7 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
     if (a < bw && b < bw && a <= b)
       for (int li = 0; li < nloc; ++li) {
         const int pi = rank + li * CS;       // panel row index
-        if (pi >= b) fmac_(acc, P[li * QB + a], P[li * QB + b]);   // pi >= b >= a
+        if (pi >= b) fmac_(acc, P[li * PS + a], P[li * PS + b]);   // pi >= b >= a
       }
     Gp[a][b] = acc;
   }
@@ -138,7 +147,7 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
     if (c >= bw) continue;
     const int pi = rank + li * CS;
     const long long gi = pb + pi;
-    const cx<R> val = P[li * QB + c];
+    const cx<R> val = P[li * PS + c];
     V[gi * ldv + pb + c] = pi >= c ? val : mk<R>(0, 0);
     A[gi * lda + pb + c] = pi < c ? val : (pi == c ? alphas[c] : mk<R>(0, 0));
   }
@@ -237,11 +246,11 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
     const int mp = m - pb;
     int cs = mp >= 512 ? 8 : (mp >= 128 ? 4 : (mp >= 32 ? 2 : 1));
     int maxloc = (mp + cs - 1) / cs;
-    size_t smem = sizeof(cx<R>) * (size_t)maxloc * QB;
+    size_t smem = sizeof(cx<R>) * (size_t)maxloc * PS;
     if (smem > 160 * 1024) {
       cs = 16;
       maxloc = (mp + cs - 1) / cs;
-      smem = sizeof(cx<R>) * (size_t)maxloc * QB;
+      smem = sizeof(cx<R>) * (size_t)maxloc * PS;
     }
     {
       ProfScope ps(st, K_QR_FACTOR);

@@ -40,6 +40,14 @@ cudaError_t fix_columns(cudaStream_t st, cx<R>* W, long long sW, int n, int r, i
 template <typename R>
 cudaError_t fix_qr(cudaStream_t st, cx<R>* Q, long long sQ, int m, int k, cx<R>* Rm, long long sR, int n, int batch);
 
+// ---- k_gemm_tc.cu (complex64 on tcgen05, split TF32)
+cudaError_t cgemm_tc(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<float> alpha, const cx<float>* A,
+                     long long sA, int lda, const cx<float>* B, long long sB, int ldb, cx<float> beta, cx<float>* C,
+                     long long sC, int ldc, int batch);
+void set_tensor_cores(int on);
+int tensor_cores_enabled();
+int* tc_error_ptr();
+
 // ---- k_linalg.cu
 // Workspace sizes (elements) for eigh_top on n x n matrices with r wanted vectors.
 struct EighWork {

@@ -238,7 +238,7 @@ nne_status move_centre(nne_state* s, int target) {
 // isometry W (n_side x r, ld r) in s->U.
 //  exact: eigenvectors of the Gram matrix X X^H (or X^H X);
 //  randomized (Halko-Martinsson-Tropp): Y = X Omega (k columns), q power
-//    iterations with re-orthonormalisation, Q = orth(Y), Rayleigh-Ritz on
+//    iterations Y <- X X^H Q each followed by re-orthonormalisation, Rayleigh-Ritz on
 //    C = (Q^H X)(Q^H X)^H, W = Q * (top-r eigenvectors of C).  Used when
 //    k < n_side; otherwise the sketch spans the space and the exact path runs.
 template <typename R>
@@ -261,9 +261,9 @@ nne_status subspace(nne_state* s, cx<R>* X, int rows, int cols, int r, int dir) 
     const int opA = dir > 0 ? OP_N : OP_C, opAh = dir > 0 ? OP_C : OP_N;
     CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Om, 0, k, zero, Y, sY, k, s->n_inst));
     CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, s->qr_ws, s->n_inst));
+    // power iterations Y <- A (A^H Q), re-orthonormalised after each application of A A^H
     for (int it = 0; it < s->power_iters; ++it) {
       CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, s->n_inst));
-      CTRY(qr<R>(st, Z, sZ, other, k, Z, sZ, nullptr, 0, s->qr_ws, s->n_inst));
       CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Z, sZ, k, zero, Y, sY, k, s->n_inst));
       CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, s->qr_ws, s->n_inst));
     }
@@ -397,12 +397,16 @@ nne_status compress(nne_state* s, int chi_new) {
 }
 
 nne_status read_err(nne_state* s) {
-  int h = 0;
+  int h = 0, t = 0;
   cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->ctx->stream);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__);
+  int* te = tc_error_ptr();
+  if (te) e = cudaMemcpyAsync(&t, te, sizeof(int), cudaMemcpyDeviceToHost, s->ctx->stream);
   if (e != cudaSuccess) return set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__);
   e = cudaStreamSynchronize(s->ctx->stream);
   if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
   if (h != 0) return set_error(h, "device-side failure status %d (non-finite or zero norm in a gate step)", h);
+  if (t != 0) return set_error(t, "tensor-core GEMM reported status %d (a bounded wait expired)", t);
   return NNE_OK;
 }
 
@@ -800,6 +804,30 @@ nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits) {
   NNE_CUDA_TRY(cudaMemsetAsync(st->d_err, 0, sizeof(int), s));
   std::fill(st->dims.begin(), st->dims.end(), 1);
   st->centre = 0;
+  return NNE_OK;
+}
+
+void nne_set_option(int option, int value) {
+  if (option == NNE_OPT_TENSOR_CORES) set_tensor_cores(value);
+}
+
+nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, const float* alpha, const void* A,
+                         int lda, long long stride_a, const void* B, int ldb, long long stride_b, const float* beta,
+                         void* C, int ldc, long long stride_c, int batch) {
+  if (!ctx || !alpha || !beta || !A || !B || !C || M < 0 || N < 0 || K < 0 || batch < 0 || op_a < 0 || op_a > 1 ||
+      op_b < 0 || op_b > 1)
+    return set_error(NNE_ERR_ARG, "nne_cgemm_c64: bad arguments");
+  DeviceGuard dg(ctx->device);
+  cudaError_t e = cgemm<float>(ctx->stream, op_a, op_b, M, N, K, mk<float>(alpha[0], alpha[1]),
+                               reinterpret_cast<const cx<float>*>(A), stride_a, lda,
+                               reinterpret_cast<const cx<float>*>(B), stride_b, ldb, mk<float>(beta[0], beta[1]),
+                               reinterpret_cast<cx<float>*>(C), stride_c, ldc, batch);
+  if (e != cudaSuccess) return set_cuda_error(e, "nne_cgemm_c64", __FILE__, __LINE__);
+  int t = 0;
+  int* te = tc_error_ptr();
+  if (te) NNE_CUDA_TRY(cudaMemcpyAsync(&t, te, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  NNE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (t != 0) return set_error(t, "tensor-core GEMM reported status %d", t);
   return NNE_OK;
 }
 

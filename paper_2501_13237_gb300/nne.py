@@ -29,7 +29,7 @@ SYMBOLS = (
     "nne_create_state", "nne_destroy_state", "nne_set_sketch", "nne_apply_layer", "nne_truncate", "nne_expect",
     "nne_extrapolate", "nne_sync", "nne_state_info", "nne_state_read_site", "nne_state_write_site",
     "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
-    "nne_extrapolate_noalloc",
+    "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
 )
 
 
@@ -76,6 +76,9 @@ def load(path: str = LIB_PATH):
         "nne_prof_enable": (None, [i32]),
         "nne_prof_collect": (i32, [vp, vp, vp, i32]),
         "nne_extrapolate_noalloc": (i32, [vp, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp]),
+        "nne_cgemm_c64": (i32, [vp, i32, i32, i32, i32, i32, vp, vp, i32, C.c_longlong, vp, i32, C.c_longlong,
+                                vp, vp, i32, C.c_longlong, i32]),
+        "nne_set_option": (None, [i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -177,6 +180,29 @@ class Context:
         _check(load().nne_extrapolate_noalloc(self.h, nl, _hptr(lam), _hptr(vals), _hptr(lf), no, method, degree,
                                               float(lambda_star), _hptr(yz), _hptr(out), _hptr(st)))
         return out, st
+
+
+    def cgemm(self, op_a: int, op_b: int, A, B, Cout, alpha=1.0, beta=0.0):
+        """Cout[z] = alpha op(A[z]) op(B[z]) + beta Cout[z] on torch complex64 CUDA tensors (batch, rows, cols)."""
+        al = np.array([complex(alpha).real, complex(alpha).imag], np.float32)
+        be = np.array([complex(beta).real, complex(beta).imag], np.float32)
+        M, N = Cout.shape[1], Cout.shape[2]
+        K = A.shape[2] if op_a == 0 else A.shape[1]
+        _check(load().nne_cgemm_c64(self.h, op_a, op_b, M, N, K, _hptr(al), _vp(A), A.shape[2],
+                                    A.shape[1] * A.shape[2], _vp(B), B.shape[2], B.shape[1] * B.shape[2],
+                                    _hptr(be), _vp(Cout), Cout.shape[2], Cout.shape[1] * Cout.shape[2],
+                                    A.shape[0]))
+
+
+def _vp(t):
+    return C.c_void_p(_dptr(t))
+
+
+def set_option(option: int, value: int):
+    load().nne_set_option(option, value)
+
+
+OPT_TENSOR_CORES = 0
 
 
 class State:

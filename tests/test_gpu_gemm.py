@@ -1,0 +1,50 @@
+"""The complex64 GEMM used by every gate step (tcgen05 split-TF32 for large
+shapes, float32 SIMT otherwise) against a float64 product of the same inputs."""
+import numpy as np
+import pytest
+
+from tests.gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = require_gpu()
+    from paper_2501_13237_gb300 import nne
+    return torch, nne, nne.Context(0)
+
+
+def crand(rng, shape):
+    return ((rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2)).astype(np.complex64)
+
+
+def op(a, o):
+    return a if o == 0 else np.conj(np.swapaxes(a, -1, -2))
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+@pytest.mark.parametrize("opa,opb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+@pytest.mark.parametrize("M,N,K", [(200, 150, 77), (128, 128, 16), (256, 384, 512), (65, 300, 33), (512, 64, 1024)])
+def test_cgemm_vs_float64(env, tc, opa, opb, M, N, K):
+    torch, nne, ctx = env
+    nne.set_option(nne.OPT_TENSOR_CORES, tc)
+    rng = np.random.default_rng(M + 7 * N + 13 * K + opa + 2 * opb)
+    batch = 2
+    A = crand(rng, (batch, M, K) if opa == 0 else (batch, K, M))
+    B = crand(rng, (batch, K, N) if opb == 0 else (batch, N, K))
+    C0 = crand(rng, (batch, M, N))
+    alpha, beta = 0.7 - 0.2j, (0.3 + 0.1j if K % 2 else 0.0)
+    dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C0))
+    ctx.cgemm(opa, opb, dA, dB, dC, alpha, beta)
+    got = dC.cpu().numpy().astype(np.complex128)
+    ref = alpha * (op(A.astype(np.complex128), opa) @ op(B.astype(np.complex128), opb)) + beta * C0
+    scale = np.sqrt(K) * np.abs(alpha)
+    err = np.abs(got - ref).max() / scale
+    nne.set_option(nne.OPT_TENSOR_CORES, 1)
+    # Error per unit sqrt(K) grows linearly in K for both paths: float32 FMA
+    # chains (~7e-6 at K = 1024) and, ~8x larger, the tensor cores' float32
+    # accumulation in tensor memory, whose additions truncate (5.5e-5 at K = 1024
+    # measured on GB300).  A layout or descriptor error would give O(1).
+    tol = (1e-5 + 6.5e-8 * K) if tc else (3e-6 + 8e-9 * K)
+    assert err < tol, err
