@@ -68,7 +68,7 @@ namespace nne {
 // Kernel classes for launch accounting / event timing (nne_prof_collect).
 enum ProfClass {
   K_GEMM = 0, K_SUPEROP_APPLY = 1, K_TRIDIAG = 2, K_BISECT = 3, K_INVITER = 4, K_BACKTRANSFORM = 5,
-  K_QR_FACTOR = 6, K_QR_FORMQ = 7, K_ELEMWISE = 8, K_SWEEP_ENV = 9, K_SWEEP_OBS = 10, K_SUPEROP_BUILD = 11,
+  K_QR_FACTOR = 6, K_WY = 7, K_ELEMWISE = 8, K_SWEEP_ENV = 9, K_SWEEP_OBS = 10, K_SUPEROP_BUILD = 11,
   K_FIT = 12, PROF_CLASSES = 16
 };
 class ProfScope {

@@ -262,8 +262,8 @@ cudaError_t tridiag_smem(cudaStream_t st, const cx<R>* H, long long sH, int n, R
 
 template <typename R>
 cudaError_t backtransform_wy(cudaStream_t st, const cx<R>* Vh, long long sVh, int n, const R* Z, long long sZ,
-                             const cx<R>* phi, int ldde, int r, cx<R>* U, long long sU, cx<R>* Tw, cx<R>* W,
-                             cx<R>* W2, int batch) {
+                             const cx<R>* phi, int ldde, int r, cx<R>* U, long long sU, cx<R>* Tw, cx<R>* wy_ws,
+                             int batch) {
   cudaError_t e;
   {
     ProfScope ps(st, K_BACKTRANSFORM);
@@ -281,19 +281,14 @@ cudaError_t backtransform_wy(cudaStream_t st, const cx<R>* Vh, long long sVh, in
     wy_t_kernel<R><<<dim3(nb, batch), 256, 0, st>>>(Vh, sVh, n, nref, Tw, sT);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const cx<R> one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
-  const long long sW = 32LL * r;
   for (int b = nb - 1; b >= 0; --b) {
     const int j0 = 32 * b, bw = std::min(32, nref - j0);
     const int r0 = j0 + 1, mb = n - r0;
     const cx<R>* Vb = Vh + (long long)j0 * n + r0;    // bw x mb, rows = conj(v)
     cx<R>* Ub = U + (long long)r0 * r;
-    if ((e = cgemm<R>(st, OP_N, OP_N, bw, r, mb, one, Vb, sVh, n, Ub, sU, r, zero, W, sW, r, batch)) != cudaSuccess)
-      return e;
-    if ((e = cgemm<R>(st, OP_N, OP_N, bw, r, bw, one, Tw + (long long)b * 1024, sT, 32, W, sW, r, zero, W2, sW, r,
-                      batch)) != cudaSuccess)
-      return e;
-    if ((e = cgemm<R>(st, OP_C, OP_N, mb, r, bw, mone, Vb, sVh, n, W2, sW, r, one, Ub, sU, r, batch)) != cudaSuccess)
+    // U_b <- (I - V T V^H) U_b
+    if ((e = wy_apply<R>(st, true, Vb, sVh, n, Tw + (long long)b * 1024, sT, 32, false, bw, mb, r, Ub, sU, r, wy_ws,
+                         batch)) != cudaSuccess)
       return e;
   }
   return cudaSuccess;
@@ -304,7 +299,7 @@ cudaError_t backtransform_wy(cudaStream_t st, const cx<R>* Vh, long long sVh, in
   template cudaError_t tridiag_smem<R>(cudaStream_t, const cx<R>*, long long, int, R*, cx<R>*, int, cx<R>*,    \
                                        long long, int);                                                         \
   template cudaError_t backtransform_wy<R>(cudaStream_t, const cx<R>*, long long, int, const R*, long long,    \
-                                           const cx<R>*, int, int, cx<R>*, long long, cx<R>*, cx<R>*, cx<R>*, int);
+                                           const cx<R>*, int, int, cx<R>*, long long, cx<R>*, cx<R>*, int);
 NNE_INST_EIGS(float)
 NNE_INST_EIGS(double)
 

@@ -366,9 +366,10 @@ static int cluster_size_for(int n) { return n >= 512 ? 8 : (n >= 128 ? 4 : (n >=
 EighWork eigh_workspace(int n, int r) {
   EighWork w;
   const long long qn = std::max(n, r);
-  // cx: e, phi, P (n each), Vh (n x n), WY factors (ceil(n/32) x 32 x 32), W, W2 (32 x r each),
-  //     QR workspace of an n x r matrix
-  w.cx_elems = 3LL * n + (long long)n * n + ((n + 31) / 32) * 1024LL + 64LL * r + qr_workspace(n, r).cx_elems + 32;
+  // cx: e, phi, P (n each), Vh (n x n), WY factors (ceil(n/32) x 32 x 32), WY application workspace
+  //     (for r columns), QR workspace of an n x r matrix
+  w.cx_elems = 3LL * n + (long long)n * n + ((n + 31) / 32) * 1024LL + wy_workspace(r) + qr_workspace(n, r).cx_elems +
+               32;
   // re: d, eabs (n each), lam (r), Z (n r), L/U0/U1/U2 (4 n r), Kpart (32 doubles = 64 floats)
   w.re_elems = 2LL * n + r + 5LL * n * r + 64 + qn;
   w.u8_elems = (long long)n * r;
@@ -392,9 +393,8 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
   cx<R>* Vh = P + (long long)batch * n;             // batch x n x n
   cx<R>* Tw = Vh + (long long)batch * n * n;        // batch x nb x 1024
   const int nbw = (n + 31) / 32;
-  cx<R>* W = Tw + (long long)batch * nbw * 1024;    // batch x 32 r
-  cx<R>* W2 = W + (long long)batch * 32 * r;
-  cx<R>* qrws = W2 + (long long)batch * 32 * r;     // QR workspace for batch n x r matrices
+  cx<R>* wyws = Tw + (long long)batch * nbw * 1024;          // batch x wy_workspace(r)
+  cx<R>* qrws = wyws + (long long)batch * wy_workspace(r);   // QR workspace for batch n x r matrices
   R* d = reb;                                       // batch x n
   R* eabs = d + (long long)batch * n;               // batch x n
   R* lam = eabs + (long long)batch * n;             // batch x r
@@ -435,7 +435,7 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
                                                            sS, total);
   }
   if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
-  ce = backtransform_wy<R>(st, Vh, (long long)n * n, n, Z, sS, phi, ldde, r, U, sU, Tw, W, W2, batch);
+  ce = backtransform_wy<R>(st, Vh, (long long)n * n, n, Z, sS, phi, ldde, r, U, sU, Tw, wyws, batch);
   if (ce != cudaSuccess) return ce;
   // orthonormalise the eigenvector block (QR; Q written over U)
   return qr<R>(st, U, sU, n, r, U, sU, nullptr, 0, qrws, batch);

@@ -5,8 +5,8 @@
 // shared memory; per column the cluster exchanges two partial reductions
 // (column norm, reflector projections) through distributed shared memory.
 // Each panel also yields the compact-WY factor T (P_0 ... P_{b-1} =
-// I - V T V^H).  Trailing updates and the explicit Q are then three GEMMs
-// per panel.  All reductions are in a fixed order (deterministic).
+// I - V T V^H).  Trailing updates and the explicit Q then apply each panel's
+// block reflector (wy_apply).  All reductions are in a fixed order (deterministic).
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -221,8 +221,8 @@ QrWork qr_workspace(int m, int n) {
   QrWork w;
   const int k = std::min(m, n);
   const int np = (k + QB - 1) / QB;
-  // V (m x n) + T (np x 32 x 32) + W, W2 (32 x n each)
-  w.cx_elems = (long long)m * n + (long long)np * QB * QB + 2LL * QB * n + 64;
+  // V (m x n) + T (np x 32 x 32) + WY application workspace (n columns)
+  w.cx_elems = (long long)m * n + (long long)np * QB * QB + wy_workspace(n) + 64;
   return w;
 }
 
@@ -236,10 +236,7 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
   const long long sV = (long long)m * n;
   cx<R>* T = V + sV * batch;
   const long long sT = (long long)np * QB * QB;
-  cx<R>* W = T + sT * batch;
-  const long long sW = (long long)QB * n;
-  cx<R>* W2 = W + sW * batch;
-  const cx<R> one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
+  cx<R>* wyws = T + sT * batch;
   cudaError_t e;
   for (int p = 0; p < np; ++p) {
     const int pb = p * QB, bw = std::min(QB, k - pb);
@@ -262,12 +259,9 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
     if (nt > 0) {
       cx<R>* Vp = V + (long long)pb * n + pb;
       cx<R>* At = A + (long long)pb * n + pb + bw;
-      if ((e = cgemm<R>(st, OP_C, OP_N, bw, nt, mp, one, Vp, sV, n, At, sA, n, zero, W, sW, nt, batch)) != cudaSuccess)
-        return e;
-      if ((e = cgemm<R>(st, OP_C, OP_N, bw, nt, bw, one, T + p * QB * QB, sT, QB, W, sW, nt, zero, W2, sW, nt,
-                        batch)) != cudaSuccess)
-        return e;
-      if ((e = cgemm<R>(st, OP_N, OP_N, mp, nt, bw, mone, Vp, sV, n, W2, sW, nt, one, At, sA, n, batch)) != cudaSuccess)
+      // A_t <- (I - V T V^H)^H A_t
+      if ((e = wy_apply<R>(st, false, Vp, sV, n, T + p * QB * QB, sT, QB, true, bw, mp, nt, At, sA, n, wyws,
+                           batch)) != cudaSuccess)
         return e;
     }
   }
@@ -282,12 +276,9 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
     const int mp = m - pb, kc = k - pb;
     cx<R>* Vp = V + (long long)pb * n + pb;
     cx<R>* Qp = Q + (long long)pb * k + pb;
-    if ((e = cgemm<R>(st, OP_C, OP_N, bw, kc, mp, one, Vp, sV, n, Qp, sQ, k, zero, W, sW, kc, batch)) != cudaSuccess)
-      return e;
-    if ((e = cgemm<R>(st, OP_N, OP_N, bw, kc, bw, one, T + p * QB * QB, sT, QB, W, sW, kc, zero, W2, sW, kc, batch)) !=
+    // Q_p <- (I - V T V^H) Q_p
+    if ((e = wy_apply<R>(st, false, Vp, sV, n, T + p * QB * QB, sT, QB, false, bw, mp, kc, Qp, sQ, k, wyws, batch)) !=
         cudaSuccess)
-      return e;
-    if ((e = cgemm<R>(st, OP_N, OP_N, mp, kc, bw, mone, Vp, sV, n, W2, sW, kc, one, Qp, sQ, k, batch)) != cudaSuccess)
       return e;
   }
   return cudaSuccess;

@@ -70,8 +70,19 @@ cudaError_t tridiag_smem(cudaStream_t st, const cx<R>* H, long long sH, int n, R
                          long long sVh, int batch);
 template <typename R>
 cudaError_t backtransform_wy(cudaStream_t st, const cx<R>* Vh, long long sVh, int n, const R* Z, long long sZ,
-                             const cx<R>* phi, int ldde, int r, cx<R>* U, long long sU, cx<R>* Tw, cx<R>* W,
-                             cx<R>* W2, int batch);
+                             const cx<R>* phi, int ldde, int r, cx<R>* U, long long sU, cx<R>* Tw, cx<R>* wy_ws,
+                             int batch);
+
+// ---- k_wy.cu
+// C[z] <- C[z] - V op(T) V^H C[z] for bw <= 32 Householder vectors in compact-WY
+// form (op(T) = T^H if t_adj).  V is K x bw with rows at V + i * ldv, or, if
+// v_rows, given as V^H (bw x K, rows at V + c * ldv).  T is bw x bw (ld ldt),
+// C is K x N (ld ldc).  ws holds batch * wy_workspace(N) elements.
+long long wy_workspace(int N);
+template <typename R>
+cudaError_t wy_apply(cudaStream_t st, bool v_rows, const cx<R>* V, long long sV, int ldv, const cx<R>* T,
+                     long long sT, int ldt, bool t_adj, int bw, int K, int N, cx<R>* C, long long sC, int ldc,
+                     cx<R>* ws, int batch);
 
 struct QrWork {
   long long cx_elems;

@@ -282,7 +282,7 @@ class State:
 
 
 PROF_CLASSES = ("gemm", "superop_epilogue", "tridiag", "bisect", "inviter", "backtransform", "qr_factor",
-                "qr_formq", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit")
+                "wy_apply", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit")
 
 
 def kernel_launches() -> int:
