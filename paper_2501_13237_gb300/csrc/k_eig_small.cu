@@ -5,7 +5,8 @@
 // Reduction: rows are spread cyclically over the CTAs of a cluster and stay
 // in shared memory for the whole reduction; column j is read from its owner
 // through distributed shared memory, every CTA forms the Householder vector
-// redundantly (identical arithmetic, so identical results), the products
+// redundantly (identical arithmetic, so identical results; the FP64 parts on
+// one thread per CTA), the products
 // p = A v are pushed to every CTA, and one more barrier closes the rank-2
 // update.  Reflector j is stored conjugated as row j of Vh (n x n).
 #include "kernels.cuh"
@@ -13,17 +14,6 @@
 namespace cg = cooperative_groups;
 
 namespace nne {
-
-template <typename T>
-__device__ __forceinline__ T bsum(T v, T* red) {
-  v = warp_sum_r(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  T t = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-  return t;
-}
 
 template <typename R>
 __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long long sH, int n, R* db, cx<R>* eb,
@@ -44,12 +34,16 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
   __shared__ double ks[2][16];                        // K partials pushed by every CTA
   __shared__ R dpush[2];                              // diagonal entry pushed with the column
   __shared__ double red[32];
+  __shared__ cx<R> alpha_s;
+  __shared__ R inv_s, twoK_s;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
   const int nloc = n > rank ? (n - rank + CS - 1) / CS : 0;
   for (long long e2 = tid; e2 < (long long)nloc * n; e2 += nth) {
     const int li = (int)(e2 / n), c = (int)(e2 % n);
     Hl[e2] = H[(long long)(rank + li * CS) * n + c];
   }
+  // every CTA of the cluster is running before anyone writes into its shared memory
+  cluster.sync();
   // column 0 below the diagonal = conj(row 0 tail), pushed by the owner of row 0
   if (rank == 0) {
     for (int t = tid; t + 1 < n; t += nth) {
@@ -63,21 +57,35 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
     const int m = n - j - 1, owner = j % CS, buf = j & 1;
     cx<R>* v = vbuf + buf * n;
     const R djj = dpush[buf];
-    // Householder vector (every CTA, same arithmetic)
-    double s = 0;
-    for (int t = tid; t < m; t += nth) s += (double)norm2(v[t]);
-    const double xn2 = bsum(s, red);
-    const cx<R> x0 = v[0];
-    const double ax0 = sqrt((double)norm2(x0)), xn = sqrt(xn2);
-    cx<R> alpha = mk<R>(0, 0);
-    double un = 0;
-    if (xn > 0) {
-      const double pr = ax0 > 0 ? (double)x0.re / ax0 : 1.0, pi = ax0 > 0 ? (double)x0.im / ax0 : 0.0;
-      alpha = mk<R>((R)(-xn * pr), (R)(-xn * pi));
-      un = sqrt(2.0 * xn2 + 2.0 * xn * ax0);
+    // Householder vector (every CTA, same arithmetic).  Squared norm: per-warp
+    // partials in R, combined in FP64 by one thread, which also forms alpha and
+    // 1/un (FP64 is slow on this part: keep it off the other threads).
+    {
+      R sp = 0;
+      for (int t = tid; t < m; t += nth) sp += norm2(v[t]);
+      sp = warp_sum_r(sp);
+      if (lane == 0) red[warp] = (double)sp;
     }
     __syncthreads();
-    const R inv = un > 0 ? (R)(1.0 / un) : R(0);
+    if (tid == 0) {
+      double xn2 = 0;
+      for (int w2 = 0; w2 < nw; ++w2) xn2 += red[w2];
+      const cx<R> x0 = v[0];
+      const double ax0 = sqrt((double)norm2(x0)), xn = sqrt(xn2);
+      cx<R> alpha = mk<R>(0, 0);
+      double un = 0;
+      if (xn > 0) {
+        const double pr = ax0 > 0 ? (double)x0.re / ax0 : 1.0, pi = ax0 > 0 ? (double)x0.im / ax0 : 0.0;
+        alpha = mk<R>((R)(-xn * pr), (R)(-xn * pi));
+        un = sqrt(2.0 * xn2 + 2.0 * xn * ax0);
+      }
+      alpha_s = alpha;
+      inv_s = un > 0 ? (R)(1.0 / un) : R(0);
+      if (rank == owner) { d[j] = djj; e[j] = alpha; }
+    }
+    __syncthreads();
+    const cx<R> alpha = alpha_s;
+    const R inv = inv_s;
     for (int t = tid; t < m; t += nth) {
       cx<R> u = v[t];
       if (t == 0) u = u - alpha;
@@ -85,13 +93,12 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
     }
     __syncthreads();
     if (rank == owner) {
-      if (tid == 0) { d[j] = djj; e[j] = alpha; }
       cx<R>* vr = Vh + (long long)j * n + (j + 1);
       for (int t = tid; t < m; t += nth) vr[t] = conj(v[t]);
     }
     // p = A v on own rows i >= j+1, pushed to every CTA
     const int lstart = (j + 1 - rank + CS - 1) / CS;
-    double kp = 0;
+    R kp = 0;
     for (int li = lstart + warp; li < nloc; li += nw) {
       const int i = rank + li * CS, t = i - j - 1;
       const cx<R>* row = Hl + (long long)li * n + (j + 1);
@@ -107,14 +114,23 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
       cx<R> acc = (a0 + a1) + (a2 + a3);
       acc = warp_sum(acc);
       if (lane < CS) *cluster.map_shared_rank(p + t, lane) = acc;
-      if (lane == 0) kp += (double)v[t].re * acc.re + (double)v[t].im * acc.im;
+      if (lane == 0) kp += v[t].re * acc.re + v[t].im * acc.im;
     }
-    kp = bsum(kp, red);
-    if (tid < CS) *cluster.map_shared_rank(&ks[buf][rank], tid) = kp;
+    if (lane == 0) red[warp] = (double)kp;
+    __syncthreads();
+    if (tid < CS) {
+      double t = 0;
+      for (int w2 = 0; w2 < nw; ++w2) t += red[w2];
+      *cluster.map_shared_rank(&ks[buf][rank], tid) = t;
+    }
     cluster.sync();
-    double K = 0;
-    for (int c = 0; c < CS; ++c) K += ks[buf][c];
-    const R twoK = (R)(2.0 * K);
+    if (tid == 0) {
+      double K = 0;
+      for (int c = 0; c < CS; ++c) K += ks[buf][c];
+      twoK_s = (R)(2.0 * K);
+    }
+    __syncthreads();
+    const R twoK = twoK_s;
     for (int t = tid; t < m; t += nth) w[t] = mk<R>(2 * p[t].re - twoK * v[t].re, 2 * p[t].im - twoK * v[t].im);
     __syncthreads();
     for (int li = lstart + warp; li < nloc; li += nw) {

@@ -161,24 +161,55 @@ __global__ void __launch_bounds__(256) tridiag_kernel(cx<R>* Hb, long long sH, i
 }
 
 // |e_k| and the phases phi (phi_0 = 1, phi_{k+1} = phi_k e_k/|e_k|) that make
-// the tridiagonal real: T = D T' D^H with T'_{k+1,k} = |e_k|.
+// the tridiagonal real: T = D T' D^H with T'_{k+1,k} = |e_k|.  One CTA per
+// matrix: each thread multiplies the unit phases of a contiguous chunk, a
+// block-wide scan (FP64, fixed order) gives every chunk its prefix.
+__device__ __forceinline__ cx<double> shfl_up_cd(cx<double> v, int d) {
+  return mk<double>(__shfl_up_sync(0xffffffffu, v.re, d), __shfl_up_sync(0xffffffffu, v.im, d));
+}
+__device__ __forceinline__ cx<double> unit_phase(double er, double ei, double* a) {
+  const double a2 = er * er + ei * ei;
+  *a = sqrt(a2);
+  if (!(a2 > 0)) return mk<double>(1.0, 0.0);
+  const double inv = 1.0 / *a;
+  return mk<double>(er * inv, ei * inv);
+}
 template <typename R>
-__global__ void tridiag_phases_kernel(const cx<R>* eb, int n, int ldde, R* eabs, cx<R>* phib, int batch) {
-  const int z = blockIdx.x * blockDim.x + threadIdx.x;
-  if (z >= batch) return;
+__global__ void __launch_bounds__(256) tridiag_phases_kernel(const cx<R>* eb, int n, int ldde, R* eabs,
+                                                             cx<R>* phib) {
+  __shared__ cx<double> wtot[8];
+  const int z = blockIdx.x;
   const cx<R>* e = eb + (long long)z * ldde;
   R* ea = eabs + (long long)z * ldde;
   cx<R>* phi = phib + (long long)z * ldde;
+  const int m = n - 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int chunk = m > 0 ? (m + 255) / 256 : 0;
+  const int k0 = min(m, tid * chunk), k1 = min(m, k0 + chunk);
   cx<double> p = mk<double>(1.0, 0.0);
-  phi[0] = mk<R>(1, 0);
-  for (int k = 0; k + 1 < n; ++k) {
-    const double er = e[k].re, ei = e[k].im;
-    const double a = sqrt(er * er + ei * ei);
+  for (int k = k0; k < k1; ++k) {
+    double a;
+    p = p * unit_phase((double)e[k].re, (double)e[k].im, &a);
     ea[k] = (R)a;
-    if (a > 0) p = p * mk<double>(er / a, ei / a);
-    const double pa = sqrt(p.re * p.re + p.im * p.im);
-    p = mk<double>(p.re / pa, p.im / pa);
-    phi[k + 1] = mk<R>((R)p.re, (R)p.im);
+  }
+  // inclusive scan within the warp, then over the warp totals
+  for (int d = 1; d < 32; d <<= 1) {
+    const cx<double> t = shfl_up_cd(p, d);
+    if (lane >= d) p = t * p;
+  }
+  if (lane == 31) wtot[wid] = p;
+  __syncthreads();
+  cx<double> pre = mk<double>(1.0, 0.0);
+  for (int w = 0; w < wid; ++w) pre = pre * wtot[w];
+  cx<double> excl = shfl_up_cd(p, 1);
+  if (lane == 0) excl = mk<double>(1.0, 0.0);
+  cx<double> q = pre * excl;
+  const double qa = sqrt(q.re * q.re + q.im * q.im);
+  q = mk<double>(q.re / qa, q.im / qa);
+  if (tid == 0) phi[0] = mk<R>(1, 0);
+  for (int k = k0; k < k1; ++k) {
+    double a;
+    q = q * unit_phase((double)e[k].re, (double)e[k].im, &a);
+    phi[k + 1] = mk<R>((R)q.re, (R)q.im);
   }
 }
 
@@ -419,7 +450,7 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
   if (ce != cudaSuccess) return ce;
   {
     ProfScope ps(st, K_ELEMWISE);
-    tridiag_phases_kernel<R><<<(batch + 63) / 64, 64, 0, st>>>(e, n, ldde, eabs, phi, batch);
+    tridiag_phases_kernel<R><<<batch, 256, 0, st>>>(e, n, ldde, eabs, phi);
   }
   if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
   const int total = batch * r;

@@ -2,10 +2,9 @@
 //
 // Panels of 32 columns are factored by one thread-block cluster per matrix:
 // the panel rows are spread over the cluster's CTAs (cyclically) and kept in
-// shared memory; per column the cluster exchanges two partial reductions
-// (column norm, reflector projections) through distributed shared memory.
-// Each panel also yields the compact-WY factor T (P_0 ... P_{b-1} =
-// I - V T V^H).  Trailing updates and the explicit Q then apply each panel's
+// shared memory; per column the cluster exchanges one round of partial sums
+// through distributed shared memory.  Each panel also yields the compact-WY
+// factor T (P_0 ... P_{b-1} = I - V T V^H).  Trailing updates and the explicit Q then apply each panel's
 // block reflector (wy_apply).  All reductions are in a fixed order (deterministic).
 #include "kernels.cuh"
 
@@ -16,10 +15,37 @@ namespace nne {
 constexpr int QB = 32;   // panel width
 constexpr int PS = QB + 1;   // padded row stride of the shared-memory panel (avoids bank conflicts)
 
+constexpr int QR_THREADS = 512;
+constexpr int QR_WARPS = QR_THREADS / 32;
+constexpr int QR_CS_MAX = 16;
+
+// a - v * w, evaluated the same way wherever it is used (the owner of a row
+// and every CTA predicting that row's next pivot must agree bit for bit)
 template <typename R>
-__global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, int lda, int m, int pb, int bw,
-                                                        cx<R>* Vb, long long sV, int ldv, cx<R>* Tb, long long sT,
-                                                        int maxloc) {
+__device__ __forceinline__ cx<R> hh_upd(cx<R> a, cx<R> v, cx<R> w) {
+  return mk<R>(fma(-v.re, w.re, fma(v.im, w.im, a.re)), fma(-v.re, w.im, fma(-v.im, w.re, a.im)));
+}
+
+// One round's contribution of a CTA to the cluster-wide sums.
+template <typename R>
+struct QrMsg {
+  cx<R> w[QB];   // c < j: v_c^H v_j ; c > j: v_j^H a_c (partials over own rows)
+  cx<R> ex[3];   // a_j[j+1] (owner of row j), v_{j+1} and a_{j+1}[j+1] (owner of row j+1); 0 elsewhere
+  double nrm;    // partial squared norm of the next pivot column
+};
+
+// Factor the panel A[pb:m, pb:pb+bw] (bw <= 32) of matrix z = blockIdx.y.
+// Column j takes one cluster barrier: every CTA pushes its partial sums into
+// every CTA's shared memory, then all sum them in rank order.  The squared
+// norm of column j+1 below row j is downdated from the same round (the
+// reflector is unitary on rows >= j: ||a'_{j+1}||^2 over rows > j equals the
+// pre-update norm over rows >= j minus |a'_j[j+1]|^2); when that cancels
+// more than half of it, an extra round recomputes it.  The compact-WY factor
+// T is built column by column from the v_c^H v_j of the same rounds.
+template <typename R>
+__global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(cx<R>* Ab, long long sA, int lda, int m, int pb, int bw,
+                                                               cx<R>* Vb, long long sV, int ldv, cx<R>* Tb,
+                                                               long long sT, int maxloc) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -29,53 +55,38 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
   cx<R>* T = Tb + z * sT;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);       // [maxloc][PS]
-  __shared__ double pn[2];
-  __shared__ cx<R> x0s[2];
-  __shared__ cx<R> pw[2][QB];
-  __shared__ cx<R> red[8][QB];
-  __shared__ cx<R> Gp[QB][QB];
+  __shared__ QrMsg<R> msg[2][QR_CS_MAX];
+  __shared__ cx<R> red[QR_WARPS][QB];
+  __shared__ double redn[QR_WARPS];
+  __shared__ cx<R> wfull[QB];
+  __shared__ cx<R> gcol[QB];
   __shared__ cx<R> alphas[QB];
-  __shared__ R taus[QB];
-  __shared__ double dred[32];
-  const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+  __shared__ cx<R> Ts[QB][QB + 1];
+  __shared__ cx<R> ex_s[3];
+  __shared__ double nrm_s;
+  __shared__ cx<R> x0_s;
+  __shared__ double xn2_s;
+  __shared__ int recompute_s;
+  __shared__ cx<R> alpha_s;
+  __shared__ R inv_s, tau_s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int mp = m - pb;                                   // panel rows
   const int nloc = mp > rank ? (mp - rank + CS - 1) / CS : 0;
-  // load own rows (global row pb + rank + li*CS)
-  for (int e = tid; e < nloc * QB; e += blockDim.x) {
+  for (int e = tid; e < nloc * QB; e += QR_THREADS) {
     const int li = e / QB, c = e % QB;
     const long long gi = pb + rank + (long long)li * CS;
     P[li * PS + c] = c < bw ? A[gi * lda + pb + c] : mk<R>(0, 0);
   }
-  __syncthreads();
-  for (int j = 0; j < bw; ++j) {
-    const int buf = j & 1;
-    const int owner = j % CS;                 // CTA owning panel row j
-    const int ljo = j / CS;                   // its local index
-    // first local row with panel index >= j
-    const int lstart = (j - rank + CS - 1) / CS > 0 ? (j - rank + CS - 1) / CS : 0;
-    double s = 0;
-    for (int li = lstart + tid; li < nloc; li += blockDim.x) s += (double)norm2(P[li * PS + j]);
-    s = warp_sum_r(s);
-    if (lane == 0) dred[grp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += dred[w];
-      pn[buf] = t;
-      if (rank == owner) x0s[buf] = P[ljo * PS + j];
-    }
-    cluster.sync();
-    __shared__ double xn2s;
-    __shared__ cx<R> x0l;
-    if (tid == 0) {
-      double t2 = 0;
-      for (int c = 0; c < CS; ++c) t2 += *cluster.map_shared_rank(&pn[buf], c);
-      xn2s = t2;
-      x0l = *cluster.map_shared_rank(&x0s[buf], owner);
-    }
-    __syncthreads();
-    const double xn2 = xn2s;
-    const cx<R> x0 = x0l;
+  for (int e = tid; e < QB * QB; e += QR_THREADS) Ts[e / QB][e % QB] = mk<R>(0, 0);
+  // every CTA of the cluster is running before anyone writes into its shared memory
+  cluster.sync();
+  int round = 0;
+  // first local row whose panel row index is >= p
+  auto first_local = [&](int p) { return p > rank ? (p - rank + CS - 1) / CS : 0; };
+  // reflector of the next column from x0_s, xn2_s (one thread; FP64 is slow on this part)
+  auto pivot = [&]() {
+    const double xn2 = xn2_s;
+    const cx<R> x0 = x0_s;
     const double ax0 = sqrt((double)norm2(x0)), xn = sqrt(xn2);
     cx<R> alpha = mk<R>(0, 0);
     double un = 0;
@@ -84,65 +95,156 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
       alpha = mk<R>((R)(-xn * pr), (R)(-xn * pi));
       un = sqrt(2.0 * xn2 + 2.0 * xn * ax0);
     }
-    const R inv = un > 0 ? (R)(1.0 / un) : R(0);
-    if (tid == 0) {
-      alphas[j] = alpha;
-      taus[j] = un > 0 ? R(2) : R(0);
+    alpha_s = alpha;
+    inv_s = un > 0 ? (R)(1.0 / un) : R(0);
+    tau_s = un > 0 ? R(2) : R(0);
+  };
+  // cluster-wide squared norm of column c over panel rows >= p (one round)
+  auto norm_round = [&](int c, int p, bool with_x0) {
+    const int l0 = first_local(p);
+    R sacc = 0;
+    for (int li = l0 + tid; li < nloc; li += QR_THREADS) sacc += norm2(P[li * PS + c]);
+    sacc = warp_sum_r(sacc);
+    if (lane == 0) redn[wid] = (double)sacc;
+    __syncthreads();
+    const int buf = round & 1;
+    if (tid < CS) {
+      double t = 0;
+      for (int w = 0; w < QR_WARPS; ++w) t += redn[w];
+      QrMsg<R>* dst = cluster.map_shared_rank(&msg[buf][rank], tid);
+      dst->nrm = t;
+      cx<R> x0 = mk<R>(0, 0);
+      if (with_x0 && c < mp && rank == c % CS) x0 = P[(c / CS) * PS + c];
+      dst->ex[2] = x0;
     }
-    // v = (x - alpha e_0) / un on own rows
-    for (int li = lstart + tid; li < nloc; li += blockDim.x) {
+    cluster.sync();
+    if (tid == 0) {
+      double t = 0;
+      cx<R> x0 = mk<R>(0, 0);
+      for (int src = 0; src < CS; ++src) {
+        t += msg[buf][src].nrm;
+        x0 = x0 + msg[buf][src].ex[2];
+      }
+      xn2_s = t;
+      if (with_x0) x0_s = x0;
+      pivot();
+    }
+    ++round;
+    __syncthreads();
+  };
+  norm_round(0, 0, true);
+  for (int j = 0; j < bw; ++j) {
+    const int lstart = first_local(j);
+    const cx<R> x0 = x0_s;
+    const cx<R> alpha = alpha_s;
+    const R inv = inv_s, tau = tau_s;
+    if (tid == 0) alphas[j] = alpha;
+    const int owner = j % CS, ljo = j / CS;
+    // v = (x - alpha e_j) / un on own rows
+    for (int li = lstart + tid; li < nloc; li += QR_THREADS) {
       cx<R> u = P[li * PS + j];
       if (rank == owner && li == ljo) u = u - alpha;
       P[li * PS + j] = inv * u;
     }
     __syncthreads();
-    // partial w_c = sum conj(v_i) P[i][c], c in (j, bw)
+    const bool has_next = j + 1 < bw;
+    // partials: lane c holds v_c^H v_j (c < j) or v_j^H a_c (c > j); lane j+1 also |a_{j+1}|^2
     {
       const int c = lane;
       cx<R> acc = mk<R>(0, 0);
-      if (c > j && c < bw)
-        for (int li = lstart + grp; li < nloc; li += 8) fmac_(acc, P[li * PS + j], P[li * PS + c]);
-      red[grp][c] = acc;
-    }
-    __syncthreads();
-    if (tid < QB) {
-      cx<R> t = mk<R>(0, 0);
-      for (int g = 0; g < 8; ++g) t = t + red[g][tid];
-      pw[buf][tid] = t;
-    }
-    cluster.sync();
-    if (j + 1 < bw) {
-      // w_c over the cluster (fixed order), then P[i][c] -= 2 v_i w_c
-      __shared__ cx<R> wfull[QB];
-      if (tid < QB) {
-        cx<R> t = mk<R>(0, 0);
-        for (int cc = 0; cc < CS; ++cc) t = t + *cluster.map_shared_rank(&pw[buf][tid], cc);
-        wfull[tid] = mk<R>(2 * t.re, 2 * t.im);
-      }
-      __syncthreads();
-      for (int e = tid; e < (nloc - lstart) * QB; e += blockDim.x) {
-        const int li = lstart + e / QB, c = e % QB;
-        if (c > j && c < bw) {
-          const cx<R> vi = P[li * PS + j];
-          P[li * PS + c] = P[li * PS + c] - vi * wfull[c];
+      R nacc = 0;
+      if (c < j) {
+        for (int li = lstart + wid; li < nloc; li += QR_WARPS) fmac_(acc, P[li * PS + c], P[li * PS + j]);
+      } else if (c > j && c < bw) {
+        for (int li = lstart + wid; li < nloc; li += QR_WARPS) {
+          const cx<R> a = P[li * PS + c];
+          fmac_(acc, P[li * PS + j], a);
+          if (c == j + 1) nacc += norm2(a);
         }
       }
-      __syncthreads();
+      red[wid][c] = acc;
+      if (c == j + 1) redn[wid] = (double)nacc;
     }
-  }
-  // Gram of the reflectors (v_c zero above panel row c) -> T
-  for (int e = tid; e < QB * QB; e += blockDim.x) {
-    const int a = e / QB, b = e % QB;
-    cx<R> acc = mk<R>(0, 0);
-    if (a < bw && b < bw && a <= b)
-      for (int li = 0; li < nloc; ++li) {
-        const int pi = rank + li * CS;       // panel row index
-        if (pi >= b) fmac_(acc, P[li * PS + a], P[li * PS + b]);   // pi >= b >= a
+    __syncthreads();
+    const int buf = round & 1;
+    if (tid < QB) {
+      cx<R> t = mk<R>(0, 0);
+      for (int w = 0; w < QR_WARPS; ++w) t = t + red[w][tid];
+      for (int d = 0; d < CS; ++d) cluster.map_shared_rank(&msg[buf][rank], d)->w[tid] = t;
+    } else if (tid == QB) {
+      double nt = 0;
+      if (has_next)
+        for (int w = 0; w < QR_WARPS; ++w) nt += redn[w];
+      cx<R> e0 = mk<R>(0, 0), e1 = mk<R>(0, 0), e2 = mk<R>(0, 0);
+      if (has_next) {
+        if (rank == owner) e0 = P[ljo * PS + j + 1];
+        if (j + 1 < mp && rank == (j + 1) % CS) {
+          const int l1 = (j + 1) / CS;
+          e1 = P[l1 * PS + j];
+          e2 = P[l1 * PS + j + 1];
+        }
       }
-    Gp[a][b] = acc;
+      for (int d = 0; d < CS; ++d) {
+        QrMsg<R>* dst = cluster.map_shared_rank(&msg[buf][rank], d);
+        dst->ex[0] = e0;
+        dst->ex[1] = e1;
+        dst->ex[2] = e2;
+        dst->nrm = nt;
+      }
+    }
+    cluster.sync();
+    ++round;
+    if (tid < QB) {
+      cx<R> t = mk<R>(0, 0);
+      for (int src = 0; src < CS; ++src) t = t + msg[buf][src].w[tid];
+      if (tid > j) wfull[tid] = mk<R>(2 * t.re, 2 * t.im);
+      else wfull[tid] = mk<R>(0, 0);
+      gcol[tid] = tid < j ? t : mk<R>(0, 0);
+    } else if (tid == QB) {
+      double nt = 0;
+      cx<R> e0 = mk<R>(0, 0), e1 = mk<R>(0, 0), e2 = mk<R>(0, 0);
+      for (int src = 0; src < CS; ++src) {
+        nt += msg[buf][src].nrm;
+        e0 = e0 + msg[buf][src].ex[0];
+        e1 = e1 + msg[buf][src].ex[1];
+        e2 = e2 + msg[buf][src].ex[2];
+      }
+      nrm_s = nt;
+      ex_s[0] = e0;
+      ex_s[1] = e1;
+      ex_s[2] = e2;
+    }
+    __syncthreads();
+    // T[0:j, j] = -tau_j T[0:j, 0:j] (V^H v_j), T[j][j] = tau_j (rank 0, last warp)
+    if (rank == 0 && wid == QR_WARPS - 1) {
+      cx<R> acc = mk<R>(0, 0);
+      if (lane < j)
+        for (int l = lane; l < j; ++l) fma_(acc, Ts[lane][l], gcol[l]);
+      if (lane < j) Ts[lane][j] = mk<R>(-tau * acc.re, -tau * acc.im);
+      if (lane == j) Ts[j][j] = mk<R>(tau, 0);
+    }
+    // a_c <- a_c - v (2 v^H a_c), c in (j, bw), own rows >= j
+    if (has_next)
+      for (int e = tid; e < (nloc - lstart) * QB; e += QR_THREADS) {
+        const int li = lstart + e / QB, c = e % QB;
+        if (c > j && c < bw) P[li * PS + c] = hh_upd(P[li * PS + c], P[li * PS + j], wfull[c]);
+      }
+    if (tid == 0 && has_next) {
+      const cx<R> vj = inv * (x0 - alpha);                      // the owner's v_j, same operations
+      const cx<R> ajn = hh_upd(ex_s[0], vj, wfull[j + 1]);      // a'_j[j+1]
+      const cx<R> x0n = j + 1 < mp ? hh_upd(ex_s[2], ex_s[1], wfull[j + 1]) : mk<R>(0, 0);
+      const double nA = nrm_s;
+      const double xn2n = nA - (double)norm2(ajn);
+      x0_s = x0n;
+      xn2_s = xn2n > 0 ? xn2n : 0.0;
+      recompute_s = !(xn2n > 0.5 * nA);
+      if (!recompute_s) pivot();
+    }
+    __syncthreads();
+    if (has_next && recompute_s) norm_round(j + 1, j + 1, false);
   }
   // write back V and the R part of A
-  for (int e = tid; e < nloc * QB; e += blockDim.x) {
+  for (int e = tid; e < nloc * QB; e += QR_THREADS) {
     const int li = e / QB, c = e % QB;
     if (c >= bw) continue;
     const int pi = rank + li * CS;
@@ -151,35 +253,8 @@ __global__ void __launch_bounds__(256) qr_panel_kernel(cx<R>* Ab, long long sA, 
     V[gi * ldv + pb + c] = pi >= c ? val : mk<R>(0, 0);
     A[gi * lda + pb + c] = pi < c ? val : (pi == c ? alphas[c] : mk<R>(0, 0));
   }
-  cluster.sync();
-  if (rank == 0) {
-    __shared__ cx<R> G[QB][QB];
-    for (int e = tid; e < QB * QB; e += blockDim.x) {
-      const int a = e / QB, b = e % QB;
-      cx<R> t = mk<R>(0, 0);
-      for (int cc = 0; cc < CS; ++cc) t = t + *cluster.map_shared_rank(&Gp[a][b], cc);
-      G[a][b] = t;
-    }
-    __syncthreads();
-    if (tid < 32) {
-      // T upper triangular: T_ii = tau_i, T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i]
-      __shared__ cx<R> Ts[QB][QB];
-      for (int i = 0; i < QB; ++i) Ts[tid][i] = mk<R>(0, 0);
-      __syncwarp();
-      for (int i = 0; i < bw; ++i) {
-        const int rr = tid;
-        cx<R> acc = mk<R>(0, 0);
-        if (rr < i)
-          for (int l = rr; l < i; ++l) fma_(acc, Ts[rr][l], G[l][i]);
-        __syncwarp();
-        if (rr < i) Ts[rr][i] = mk<R>(-taus[i] * acc.re, -taus[i] * acc.im);
-        if (rr == i) Ts[i][i] = mk<R>(taus[i], 0);
-        __syncwarp();
-      }
-      for (int i = 0; i < QB; ++i) T[tid * QB + i] = Ts[tid][i];
-    }
-  }
-  cluster.sync();
+  if (rank == 0)
+    for (int e = tid; e < QB * QB; e += QR_THREADS) T[e] = Ts[e / QB][e % QB];
 }
 
 template <typename R>
@@ -204,7 +279,7 @@ static cudaError_t launch_cluster_qr(K kernel, int cs, int batch, size_t smem, c
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, batch, 1);
-  cfg.blockDim = dim3(256, 1, 1);
+  cfg.blockDim = dim3(QR_THREADS, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
