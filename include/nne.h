@@ -223,16 +223,95 @@ nne_status nne_state_set_centre(nne_state* st, int centre);
  * nne_prof_enable: when on, every launch records a CUDA event pair on its
  *   stream, grouped by kernel class; nne_prof_collect synchronises on those
  *   events, writes total milliseconds, launch counts and algorithmic work
- *   (real flops for the GEMM class, 0 where not tracked) per class (arrays of
+ *   (real flops for GEMM, reflector, QR-panel and tridiagonal classes, 0 where
+ *   not tracked) per class (arrays of
  *   n_classes, any may be NULL) and clears the record.  Returns the number of
  *   classes.
  *   Classes: 0 GEMM, 1 superoperator epilogue, 2 tridiagonal reduction,
- *   3 bisection, 4 inverse iteration, 5 back-transform, 6 QR factor,
- *   7 QR form-Q, 8 elementwise/norms, 9 environment sweep, 10 observable
- *   sweep, 11 superoperator build, 12 fit. */
+ *   3 bisection, 4 inverse iteration, 5 back-transform, 6 QR panel factor,
+ *   7 block-reflector products (split-K), 8 elementwise/norms,
+ *   9 environment sweep, 10 observable sweep, 11 superoperator build, 12 fit,
+ *   13 tensor-core GEMM (work: 8 M N K real flops per complex GEMM; class 0
+ *   is then the float32 SIMT GEMMs only). */
 long long nne_kernel_launches(void);
 void nne_prof_enable(int on);
 int nne_prof_collect(double* ms_out, long long* count_out, double* work_out, int n_classes);
+
+/* ---- Serving loop: whole extrapolation jobs, continuous batching ---------
+ *
+ * A job is the paper's problem instance [Sec. 2.2 problem statement, Sec. 3]:
+ * a circuit C on a line of qubits, a noise family N(lambda) fixed by base
+ * channel strengths scaled per level, the set of levels Lambda, observables
+ * O and the target lambda*.  The server runs each job as one state with
+ * n_lambda instances (gate steps, truncation to chi, expectation sweep) and
+ * fits the levels to lambda* on the GPU.
+ *
+ * Workers: n_workers host threads, each with its own non-blocking CUDA stream
+ * and context, take jobs from one FIFO queue, so up to n_workers jobs run on
+ * the GPU at once.  Admission: the head of the queue starts only when its
+ * device memory (nne_job_bytes) fits in what the budget has left; a job larger
+ * than the whole budget is refused by nne_submit with NNE_ERR_OOM.  Jobs do
+ * not overtake each other in admission order.
+ *
+ * Ownership: nne_submit copies everything the job points to before it
+ * returns.  nne_poll copies results into the caller's arrays of the nne_result
+ * it is given (the pointers that are not NULL) and then forgets the ticket.
+ * Errors of one job are reported in its result and do not stop the server.
+ * Calls on one server are thread-safe. */
+typedef struct nne_server nne_server;
+
+typedef struct {
+  int n_qubits;
+  int n_layers;
+  const int* layer_gates;   /* n_layers: number of gates of each layer */
+  const int* layer_dir;     /* n_layers: +1 gates applied left to right, -1 right to left */
+  const int* left_qubit;    /* sum(layer_gates): gate g acts on (left_qubit[g], left_qubit[g]+1), in order */
+  const double* U;          /* sum(layer_gates) x 4 x 4 complex128 (re, im interleaved), row-major */
+  int n_lambda;
+  const double* lambdas;    /* n_lambda noise levels */
+  const double* rates;      /* n_lambda x 4 channel strengths, as nne_build_superops */
+  int chi;
+  int dtype;                /* nne_dtype */
+  int trunc;                /* nne_trunc */
+  const void* sketch;       /* NNE_TRUNC_RSVD: sketch_rows x sketch_cols, element type of dtype, host; else NULL */
+  int sketch_rows, sketch_cols, power_iters;
+  const uint8_t* init_bits; /* n_qubits computational-basis bits, or NULL for |0...0> */
+  int n_obs;
+  const uint8_t* paulis;    /* n_obs x n_qubits Pauli codes */
+  int fit_method;           /* nne_fit */
+  int fit_degree;           /* NNE_FIT_POLY only */
+  double lambda_star;
+} nne_job;
+
+typedef struct {
+  nne_status status;        /* NNE_OK, or the error that ended the job */
+  char error[160];          /* one-line description when status != NNE_OK */
+  double* values;           /* in: caller array n_lambda x n_obs (Re <P> per level) or NULL */
+  double* log_fid;          /* in: caller array n_lambda (log of the emulation fidelity) or NULL */
+  double* estimate;         /* in: caller array n_obs (extrapolated to lambda*) or NULL */
+  int32_t* fit_status;      /* in: caller array n_obs (per-observable fit status) or NULL */
+  double t_submit, t_start, t_end;   /* seconds on the server's monotonic clock */
+  long long gate_steps;     /* gates x n_lambda applied */
+  size_t bytes_reserved;    /* device memory admitted for the job */
+} nne_result;
+
+/* flags: NNE_SERVER_DRYRUN makes workers do no GPU work at all: a job "runs"
+ * for dry_run_us microseconds and ends with status NNE_ERR_UNIMPL and no
+ * values.  It exists to test queueing and admission without a GPU. */
+#define NNE_SERVER_DRYRUN 1
+nne_status nne_server_create(int device, size_t hbm_budget_bytes, int n_workers, int flags, int dry_run_us,
+                             nne_server** out);
+/* Device memory a job needs while it runs (state, workspaces, superoperators). */
+size_t nne_job_bytes(const nne_job* job);
+nne_status nne_submit(nne_server* srv, const nne_job* job, uint64_t* ticket);
+/* NNE_OK: the job is finished and *out is filled; NNE_PENDING: not finished
+ * within timeout_ms (0 = do not wait, < 0 = wait without limit);
+ * NNE_ERR_ARG: unknown ticket. */
+nne_status nne_poll(nne_server* srv, uint64_t ticket, int timeout_ms, nne_result* out);
+/* Jobs queued, running, finished but not yet polled; bytes admitted now. */
+void nne_server_stats(nne_server* srv, int* queued, int* running, int* done, size_t* bytes_reserved);
+/* Finishes the running jobs, drops the queued ones, joins the workers. */
+void nne_server_destroy(nne_server* srv);
 
 #ifdef __cplusplus
 }

@@ -69,7 +69,7 @@ namespace nne {
 enum ProfClass {
   K_GEMM = 0, K_SUPEROP_APPLY = 1, K_TRIDIAG = 2, K_BISECT = 3, K_INVITER = 4, K_BACKTRANSFORM = 5,
   K_QR_FACTOR = 6, K_WY = 7, K_ELEMWISE = 8, K_SWEEP_ENV = 9, K_SWEEP_OBS = 10, K_SUPEROP_BUILD = 11,
-  K_FIT = 12, PROF_CLASSES = 16
+  K_FIT = 12, K_GEMM_TC = 13, PROF_CLASSES = 16
 };
 class ProfScope {
  public:
@@ -84,5 +84,10 @@ class ProfScope {
   cudaEvent_t a_, b_;
 };
 nne_status set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (and allow non-portable cluster sizes if asked).  The limit
+// only ever grows, under a lock, so launches of the same kernel with other
+// sizes from other host threads stay valid.
+cudaError_t ensure_kernel_smem(const void* func, size_t bytes, bool nonportable_cluster);
 nne_status set_error(nne_status s, const char* fmt, ...);
 }  // namespace nne

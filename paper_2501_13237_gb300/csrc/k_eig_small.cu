@@ -231,12 +231,8 @@ __global__ void __launch_bounds__(256) wy_t_kernel(const cx<R>* Vhb, long long s
 
 template <typename K, typename... Args>
 static cudaError_t launch_cl(K kernel, int cs, int batch, size_t smem, cudaStream_t st, Args... args) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_kernel_smem((const void*)kernel, smem, cs > 8);
   if (e != cudaSuccess) return e;
-  if (cs > 8) {
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, batch, 1);
   cfg.blockDim = dim3(256, 1, 1);
@@ -272,7 +268,7 @@ cudaError_t tridiag_smem(cudaStream_t st, const cx<R>* H, long long sH, int n, R
   if (cs == 0) return cudaErrorInvalidValue;
   const int maxloc = (n + cs - 1) / cs;
   const size_t smem = sizeof(cx<R>) * ((size_t)maxloc * n + 4 * (size_t)n);
-  ProfScope ps(st, K_TRIDIAG);
+  ProfScope ps(st, K_TRIDIAG, 1, 16.0 / 3.0 * (double)n * n * n * batch);   // Hermitian tridiagonalisation flops
   return launch_cl(tridiag_smem_kernel<R>, cs, batch, smem, st, H, sH, n, d, e, ldde, Vh, sVh, maxloc);
 }
 

@@ -15,6 +15,8 @@
 // accumulators and commits stage releases to mbarriers; warps 4-7 drain TMEM
 // (tcgen05.ld 32x32b) into shared memory and write C row-wise with alpha/beta.  Every mbarrier wait is bounded:
 // on expiry the kernel records an error code and leaves after freeing TMEM.
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace nne {
@@ -326,7 +328,7 @@ int tensor_cores_enabled() { return g_tc_enabled; }
 
 // Device address of the tensor-core kernels' error word (per device, looked up once).
 int* tc_error_ptr() {
-  static int* ptrs[64] = {nullptr};
+  static std::atomic<int*> ptrs[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return nullptr;
@@ -345,13 +347,8 @@ template <int OPA, int OPB>
 static cudaError_t launch_tc(cudaStream_t st, int M, int N, int K, float2 alpha, const float2* A, long long sA, int lda,
                              const float2* B, long long sB, int ldb, float2 beta, float2* C, long long sC, int ldc,
                              int batch, int* err) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(cgemm_tc_kernel<OPA, OPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e0 = ensure_kernel_smem((const void*)cgemm_tc_kernel<OPA, OPB>, tc::SMEM_BYTES, false);
+  if (e0 != cudaSuccess) return e0;
   dim3 grid((N + tc::BN - 1) / tc::BN, (M + tc::BM - 1) / tc::BM, batch);
   cgemm_tc_kernel<OPA, OPB><<<grid, 256, tc::SMEM_BYTES, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC,
                                                                 ldc, err);
@@ -364,7 +361,7 @@ cudaError_t cgemm_tc(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
   int* err = tc_error_ptr();
   if (!err) return cudaErrorInvalidSymbol;
-  ProfScope ps(st, K_GEMM, 1, 8.0 * M * N * (double)K * batch);
+  ProfScope ps(st, K_GEMM_TC, 1, 8.0 * M * N * (double)K * batch);
   const float2 al = make_float2(alpha.re, alpha.im), be = make_float2(beta.re, beta.im);
   const float2* a = reinterpret_cast<const float2*>(A);
   const float2* b = reinterpret_cast<const float2*>(B);

@@ -369,14 +369,8 @@ __global__ void inviter_kernel(const R* db, const R* eb, int n, int r, int ldde,
 // ---------------------------------------------------------------- launchers
 template <typename K, typename... Args>
 static cudaError_t launch_cluster(K kernel, int cs, int batch, size_t smem, cudaStream_t st, Args... args) {
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (cs > 8) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = ensure_kernel_smem((const void*)kernel, smem, cs > 8);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, batch, 1);
   cfg.blockDim = dim3(256, 1, 1);
@@ -443,7 +437,7 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
     ce = tridiag_smem<R>(st, H, sH, n, d, e, ldde, Vh, (long long)n * n, batch);
   } else {
     const int cs = cluster_size_for(n);
-    ProfScope ps(st, K_TRIDIAG);
+    ProfScope ps(st, K_TRIDIAG, 1, 16.0 / 3.0 * (double)n * n * n * batch);
     ce = launch_cluster(tridiag_kernel<R>, cs, batch, 2 * sizeof(cx<R>) * (size_t)n, st, H, sH, n, d, e, ldde, P, Kp,
                         Vh, (long long)n * n);
   }

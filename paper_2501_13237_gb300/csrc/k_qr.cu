@@ -271,12 +271,8 @@ __global__ void qr_extract_r2_kernel(const cx<R>* Ab, long long sA, int lda, int
 
 template <typename K, typename... Args>
 static cudaError_t launch_cluster_qr(K kernel, int cs, int batch, size_t smem, cudaStream_t st, Args... args) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_kernel_smem((const void*)kernel, smem, cs > 8);
   if (e != cudaSuccess) return e;
-  if (cs > 8) {
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, batch, 1);
   cfg.blockDim = dim3(QR_THREADS, 1, 1);
@@ -325,7 +321,11 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
       smem = sizeof(cx<R>) * (size_t)maxloc * PS;
     }
     {
-      ProfScope ps(st, K_QR_FACTOR);
+      // panel flops: per column j, reflector products and update of the bw-1-j columns to its right
+      // and the v_c^H v_j of the j columns to its left, over mp - j rows (8 real flops per complex MAC)
+      double work = 0;
+      for (int j = 0; j < bw; ++j) work += 8.0 * (double)(mp - j) * (2.0 * (bw - 1 - j) + j + 1);
+      ProfScope ps(st, K_QR_FACTOR, 1, work * batch);
       e = launch_cluster_qr(qr_panel_kernel<R>, cs, batch, smem, st, A, sA, n, m, pb, bw, V, sV, n, T + p * QB * QB,
                             sT, maxloc);
     }

@@ -188,10 +188,7 @@ cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* 
   if (e != cudaSuccess) return e;
   if (n_obs <= 0) return cudaSuccess;
   const size_t smem = 2 * sizeof(cx<double>) * (size_t)max_dim;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(obs_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  if ((e = ensure_kernel_smem((const void*)obs_kernel<R>, smem, false)) != cudaSuccess) return e;
   ProfScope ps(st, K_SWEEP_OBS);
   obs_kernel<R><<<dim3(n_obs, n_inst), 256, smem, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale,
                                                         d_paulis, d_first, d_last, n_obs, d_out);

@@ -1,6 +1,7 @@
 // Declarations of the device kernels' host launchers (all enqueue on `st`).
 #pragma once
 #include <algorithm>
+#include <vector>
 #include "common.cuh"
 
 namespace nne {
@@ -115,6 +116,12 @@ cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int 
 cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, const double* d_vals,
                             const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
                             const double* d_yzero, double* d_out, int* d_status);
+
+// ---- nne_api.cu
+// Bond capacities min(chi, 4^k, 4^(n-k)), k = 0..n.
+std::vector<int> bond_caps(int n, int chi);
+// Device bytes a state (plus its sketch buffers when sketch_cols > 0) allocates.
+size_t state_bytes(int n, int chi, int n_inst, int dtype, int sketch_rows, int sketch_cols);
 
 // Device ordinal and stream of a context (defined with the context in nne_api.cu).
 void ctx_device_stream(const nne_ctx* ctx, int* device, cudaStream_t* stream);

@@ -46,7 +46,10 @@ struct nne_ctx {
   size_t used = 0;
   ScratchF64 snoise;   // superoperator-build scratch, grown on demand
   ~nne_ctx() {
-    if (snoise.p) cudaFree(snoise.p);
+    if (snoise.p) {
+      cudaFreeAsync(snoise.p, stream);
+      cudaStreamSynchronize(stream);
+    }
   }
 };
 
@@ -68,15 +71,16 @@ struct DevAlloc {
     bytes = (bytes + 255) & ~size_t(255);
     if (ctx->budget && ctx->used + bytes > ctx->budget)
       return set_error(NNE_ERR_OOM, "HBM budget exceeded: %zu + %zu > %zu bytes", ctx->used, bytes, ctx->budget);
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc", __FILE__, __LINE__);
+    // stream-ordered: no device-wide synchronisation, so states on other streams keep running
+    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
     ctx->used += bytes;
     blocks.push_back({*p, bytes});
     return NNE_OK;
   }
   void release() {
     for (auto& b : blocks) {
-      cudaFree(b.first);
+      cudaFreeAsync(b.first, ctx->stream);
       ctx->used -= b.second;
     }
     blocks.clear();
@@ -88,19 +92,73 @@ constexpr int PARTS = 64;   // partial sums per instance for Frobenius norms
 ScratchF64& scratch_snoise(nne_ctx* ctx, int n_inst) {
   const size_t need = 512 * (size_t)n_inst;
   if (ctx->snoise.n < need) {
-    if (ctx->snoise.p) {
-      cudaStreamSynchronize(ctx->stream);
-      cudaFree(ctx->snoise.p);
-    }
+    if (ctx->snoise.p) cudaFreeAsync(ctx->snoise.p, ctx->stream);
     ctx->snoise.p = nullptr;
     ctx->snoise.n = 0;
-    if (cudaMalloc(&ctx->snoise.p, need * sizeof(double)) == cudaSuccess) ctx->snoise.n = need;
+    if (cudaMallocAsync(&ctx->snoise.p, need * sizeof(double), ctx->stream) == cudaSuccess) ctx->snoise.n = need;
     else ctx->snoise.p = nullptr;
   }
   return ctx->snoise;
 }
 
 }  // namespace
+
+namespace nne {
+// Bond capacities min(chi, 4^k, 4^(n-k)), k = 0..n.
+std::vector<int> bond_caps(int n, int chi) {
+  std::vector<int> cap(n + 1, 1);
+  for (int k = 1; k < n; ++k) {
+    long long c = chi;
+    long long p = 1;
+    for (int i = 0; i < k && p < c; ++i) p *= 4;
+    c = std::min(c, p);
+    p = 1;
+    for (int i = 0; i < n - k && p < c; ++i) p *= 4;
+    c = std::min(c, p);
+    cap[k] = (int)c;
+  }
+  return cap;
+}
+
+static size_t round256(size_t b) { return ((b == 0 ? 16 : b) + 255) & ~size_t(255); }
+
+// Device bytes nne_create_state (and nne_set_sketch, when sketch_cols > 0)
+// allocate for these arguments: the same blocks, rounded the same way.
+size_t state_bytes(int n, int chi, int n_inst, int dtype, int sketch_rows, int sketch_cols) {
+  const std::vector<int> cap = bond_caps(n, chi);
+  int dmax = 1;
+  for (int c : cap) dmax = std::max(dmax, c);
+  const size_t esz = dtype == NNE_C64 ? 8 : 16;
+  size_t total = 0;
+  size_t arena = 0;
+  for (int k = 0; k < n; ++k) {
+    arena += (size_t)cap[k] * 4 * cap[k + 1] * n_inst * esz;
+    arena = (arena + 255) & ~size_t(255);
+  }
+  total += round256(arena);
+  total += round256(sizeof(double) * (3 * (size_t)n_inst + 2 * (size_t)n_inst * PARTS) + 64);
+  const long long D = dmax, N4 = 4 * D;
+  total += round256((size_t)(N4 * N4) * n_inst * esz) * 3;     // X, H, T
+  total += round256((size_t)(N4 * D) * n_inst * esz);          // U
+  total += round256((size_t)std::max(N4 * D, D * D) * n_inst * esz);
+  const EighWork ew = eigh_workspace((int)N4, (int)D);
+  total += round256((size_t)ew.cx_elems * n_inst * esz);
+  total += round256((size_t)ew.re_elems * n_inst * (esz / 2) + 256);
+  total += round256((size_t)ew.u8_elems * n_inst);
+  total += round256((size_t)qr_workspace((int)N4, (int)N4).cx_elems * n_inst * esz);
+  total += round256(n);
+  total += round256(sizeof(int) * (n + 1)) + round256(sizeof(void*) * n) + round256(sizeof(long long) * n);
+  total += round256(sizeof(double) * 2 * 2 * (size_t)(n + 1) * D * n_inst);
+  total += round256(sizeof(double) * 2 * (size_t)(n + 1) * n_inst);
+  if (sketch_cols > 0) {
+    total += round256((size_t)sketch_rows * sketch_cols * esz);
+    total += round256((size_t)(N4 * sketch_cols) * n_inst * esz) * 2;
+    total += round256((size_t)sketch_cols * sketch_cols * n_inst * esz);
+    total += round256((size_t)sketch_cols * D * n_inst * esz);
+  }
+  return total;
+}
+}  // namespace nne
 
 struct nne_state {
   nne_ctx* ctx = nullptr;
@@ -480,9 +538,9 @@ nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_
   double *dU = nullptr, *dR = nullptr, *dS = nullptr;
   const size_t bu = sizeof(double) * 32 * (size_t)std::max(n_gates, 1), br = sizeof(double) * 4 * n_inst,
                bs = sizeof(double) * 512 * n_inst;
-  NNE_CUDA_TRY(cudaMalloc(&dU, bu));
-  NNE_CUDA_TRY(cudaMalloc(&dR, br));
-  NNE_CUDA_TRY(cudaMalloc(&dS, bs));
+  NNE_CUDA_TRY(cudaMallocAsync(&dU, bu, ctx->stream));
+  NNE_CUDA_TRY(cudaMallocAsync(&dR, br, ctx->stream));
+  NNE_CUDA_TRY(cudaMallocAsync(&dS, bs, ctx->stream));
   nne_status rc = NNE_OK;
   cudaError_t e = cudaSuccess;
   if (n_gates > 0) e = cudaMemcpyAsync(dU, U, sizeof(double) * 32 * n_gates, cudaMemcpyDefault, ctx->stream);
@@ -490,9 +548,9 @@ nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_
   if (e == cudaSuccess) e = build_superops(ctx->stream, n_gates, dU, n_inst, dR, (double*)G_out, dS);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) rc = set_cuda_error(e, "build_superops", __FILE__, __LINE__);
-  cudaFree(dU);
-  cudaFree(dR);
-  cudaFree(dS);
+  cudaFreeAsync(dU, ctx->stream);
+  cudaFreeAsync(dR, ctx->stream);
+  cudaFreeAsync(dS, ctx->stream);
   return rc;
 }
 
@@ -515,18 +573,8 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
   s->esz = dtype == NNE_C64 ? 8 : 16;
   const int n = n_qubits;
   s->dims.assign(n + 1, 1);
-  s->cap.assign(n + 1, 1);
-  for (int k = 1; k < n; ++k) {
-    long long c = chi;
-    long long p = 1;
-    for (int i = 0; i < k && p < c; ++i) p *= 4;
-    c = std::min(c, p);
-    p = 1;
-    for (int i = 0; i < n - k && p < c; ++i) p *= 4;
-    c = std::min(c, p);
-    s->cap[k] = (int)c;
-    s->dmax = std::max(s->dmax, (int)c);
-  }
+  s->cap = bond_caps(n, chi);
+  for (int k = 0; k <= n; ++k) s->dmax = std::max(s->dmax, s->cap[k]);
   auto fail = [&](nne_status rc) {
     s->mem.release();
     delete s;
@@ -563,14 +611,15 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
         }
       }
     }
-    cudaError_t e = cudaMemcpy(arena, host.data(), total, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpy", __FILE__, __LINE__));
+    cudaError_t e = cudaMemcpyAsync(arena, host.data(), total, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__));
   }
   // scalars
   void* p = nullptr;
   if ((rc = s->mem.alloc(&p, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64)) != NNE_OK)
     return fail(rc);
-  cudaMemset(p, 0, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64);
+  cudaMemsetAsync(p, 0, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64, ctx->stream);
   s->d_lognorm = reinterpret_cast<double*>(p);
   s->d_logfid = s->d_lognorm + n_inst;
   s->d_scale = s->d_logfid + n_inst;
@@ -600,8 +649,8 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
     for (int k = 0; k < n; ++k) s->bits[k] = init_bits[k] ? 1 : 0;
   if ((rc = s->mem.alloc(&p, n)) != NNE_OK) return fail(rc);
   s->d_bits = reinterpret_cast<uint8_t*>(p);
-  if (cudaMemcpy(s->d_bits, s->bits.data(), n, cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail(set_error(NNE_ERR_CUDA, "cudaMemcpy bits"));
+  if (cudaMemcpyAsync(s->d_bits, s->bits.data(), n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    return fail(set_error(NNE_ERR_CUDA, "cudaMemcpyAsync bits"));
   // sweep buffers
   if ((rc = s->mem.alloc(&p, sizeof(int) * (n + 1))) != NNE_OK) return fail(rc);
   s->d_dims = reinterpret_cast<int*>(p);
@@ -615,12 +664,12 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
   s->d_envscale = reinterpret_cast<double*>(p);
   {
     std::vector<void*> hs(s->site.begin(), s->site.end());
-    cudaError_t e = cudaMemcpy(s->d_site, hs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->d_stride, s->sstride.data(), sizeof(long long) * n, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpy", __FILE__, __LINE__));
+    cudaError_t e = cudaMemcpyAsync(s->d_site, hs.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(s->d_stride, s->sstride.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__));
   }
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaDeviceSynchronize", __FILE__, __LINE__));
   *out = s;
   return NNE_OK;
 }
@@ -645,7 +694,8 @@ nne_status nne_set_sketch(nne_state* st, const void* omega, int rows, int cols, 
   const long long N4 = 4LL * st->dmax;
   if ((rc = st->mem.alloc(&p, (size_t)rows * cols * es)) != NNE_OK) return rc;
   st->d_omega = p;
-  NNE_CUDA_TRY(cudaMemcpy(st->d_omega, omega, (size_t)rows * cols * es, cudaMemcpyHostToDevice));
+  NNE_CUDA_TRY(cudaMemcpyAsync(st->d_omega, omega, (size_t)rows * cols * es, cudaMemcpyDefault, st->ctx->stream));
+  NNE_CUDA_TRY(cudaStreamSynchronize(st->ctx->stream));
   st->rs_sY = N4 * cols;
   st->rs_sZ = N4 * cols;
   st->rs_sC = (long long)cols * cols;
@@ -713,10 +763,10 @@ nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* r
   void *dp = nullptr, *df = nullptr, *dl = nullptr, *dout = nullptr;
   const size_t bp = (size_t)std::max(n_obs, 1) * n, bf = sizeof(int) * std::max(n_obs, 1),
                bo = sizeof(double) * 2 * (size_t)std::max(n_obs, 1) * st->n_inst;
-  NNE_CUDA_TRY(cudaMalloc(&dp, bp));
-  NNE_CUDA_TRY(cudaMalloc(&df, bf));
-  NNE_CUDA_TRY(cudaMalloc(&dl, bf));
-  NNE_CUDA_TRY(cudaMalloc(&dout, bo));
+  NNE_CUDA_TRY(cudaMallocAsync(&dp, bp, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&df, bf, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dl, bf, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dout, bo, s));
   std::vector<double> hout(2 * (size_t)std::max(n_obs, 1) * st->n_inst);
   cudaError_t e = cudaMemcpyAsync(st->d_dims, st->dims.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_obs > 0) e = cudaMemcpyAsync(dp, paulis, (size_t)n_obs * n, cudaMemcpyHostToDevice, s);
@@ -737,10 +787,10 @@ nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* r
   nne_status rc = NNE_OK;
   if (e != cudaSuccess) rc = set_cuda_error(e, "nne_expect", __FILE__, __LINE__);
   if (rc == NNE_OK) rc = read_err(st);
-  cudaFree(dp);
-  cudaFree(df);
-  cudaFree(dl);
-  cudaFree(dout);
+  cudaFreeAsync(dp, s);
+  cudaFreeAsync(df, s);
+  cudaFreeAsync(dl, s);
+  cudaFreeAsync(dout, s);
   if (rc != NNE_OK) return rc;
   for (int i = 0; i < st->n_inst; ++i)
     for (int o = 0; o < n_obs; ++o) {
@@ -761,12 +811,12 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
   cudaStream_t s = ctx->stream;
   double *dl = nullptr, *dv = nullptr, *df = nullptr, *dy = nullptr, *dout = nullptr;
   int* dst = nullptr;
-  NNE_CUDA_TRY(cudaMalloc(&dl, sizeof(double) * n_lambda));
-  NNE_CUDA_TRY(cudaMalloc(&dv, sizeof(double) * n_lambda * (size_t)n_obs));
-  NNE_CUDA_TRY(cudaMalloc(&df, sizeof(double) * n_lambda));
-  NNE_CUDA_TRY(cudaMalloc(&dy, sizeof(double) * (size_t)n_obs));
-  NNE_CUDA_TRY(cudaMalloc(&dout, sizeof(double) * (size_t)n_obs));
-  NNE_CUDA_TRY(cudaMalloc(&dst, sizeof(int) * (size_t)n_obs));
+  NNE_CUDA_TRY(cudaMallocAsync(&dl, sizeof(double) * n_lambda, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dv, sizeof(double) * n_lambda * (size_t)n_obs, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&df, sizeof(double) * n_lambda, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dy, sizeof(double) * (size_t)n_obs, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dout, sizeof(double) * (size_t)n_obs, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dst, sizeof(int) * (size_t)n_obs, s));
   cudaError_t e = cudaMemcpyAsync(dl, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dv, values, sizeof(double) * n_lambda * (size_t)n_obs, cudaMemcpyHostToDevice, s);
@@ -779,12 +829,12 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
   if (e == cudaSuccess) e = cudaMemcpyAsync(per_obs_status, dst, sizeof(int) * n_obs, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   nne_status rc = e == cudaSuccess ? NNE_OK : set_cuda_error(e, "nne_extrapolate", __FILE__, __LINE__);
-  cudaFree(dl);
-  cudaFree(dv);
-  cudaFree(df);
-  cudaFree(dy);
-  cudaFree(dout);
-  cudaFree(dst);
+  cudaFreeAsync(dl, s);
+  cudaFreeAsync(dv, s);
+  cudaFreeAsync(df, s);
+  cudaFreeAsync(dy, s);
+  cudaFreeAsync(dout, s);
+  cudaFreeAsync(dst, s);
   return rc;
 }
 

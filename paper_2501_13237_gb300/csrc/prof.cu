@@ -5,6 +5,7 @@
 // times per class after synchronising.
 #include <atomic>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.cuh"
@@ -57,6 +58,35 @@ ProfScope::~ProfScope() {
       g_prof_work[cls_] += work_;
     }
   }
+}
+
+struct AttrKey {
+  const void* f;
+  int dev;
+  bool operator==(const AttrKey& o) const { return f == o.f && dev == o.dev; }
+};
+struct AttrHash {
+  size_t operator()(const AttrKey& k) const { return std::hash<const void*>()(k.f) ^ (size_t)k.dev; }
+};
+static std::mutex g_attr_mu;
+static std::unordered_map<AttrKey, std::pair<int, bool>, AttrHash> g_attr;
+
+cudaError_t ensure_kernel_smem(const void* func, size_t bytes, bool nonportable_cluster) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  auto& a = g_attr[AttrKey{func, dev}];
+  if ((int)bytes > a.first) {
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    a.first = (int)bytes;
+  }
+  if (nonportable_cluster && !a.second) {
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    a.second = true;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace nne

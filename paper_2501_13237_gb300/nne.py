@@ -30,7 +30,27 @@ SYMBOLS = (
     "nne_extrapolate", "nne_sync", "nne_state_info", "nne_state_read_site", "nne_state_write_site",
     "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
+    "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
 )
+SERVER_DRYRUN = 1
+
+
+class JobStruct(C.Structure):
+    """nne_job (include/nne.h)."""
+    _fields_ = [("n_qubits", C.c_int), ("n_layers", C.c_int), ("layer_gates", C.c_void_p),
+                ("layer_dir", C.c_void_p), ("left_qubit", C.c_void_p), ("U", C.c_void_p), ("n_lambda", C.c_int),
+                ("lambdas", C.c_void_p), ("rates", C.c_void_p), ("chi", C.c_int), ("dtype", C.c_int),
+                ("trunc", C.c_int), ("sketch", C.c_void_p), ("sketch_rows", C.c_int), ("sketch_cols", C.c_int),
+                ("power_iters", C.c_int), ("init_bits", C.c_void_p), ("n_obs", C.c_int), ("paulis", C.c_void_p),
+                ("fit_method", C.c_int), ("fit_degree", C.c_int), ("lambda_star", C.c_double)]
+
+
+class ResultStruct(C.Structure):
+    """nne_result (include/nne.h)."""
+    _fields_ = [("status", C.c_int), ("error", C.c_char * 160), ("values", C.c_void_p), ("log_fid", C.c_void_p),
+                ("estimate", C.c_void_p), ("fit_status", C.c_void_p), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_end", C.c_double), ("gate_steps", C.c_longlong),
+                ("bytes_reserved", C.c_size_t)]
 
 
 class NNEError(RuntimeError):
@@ -79,6 +99,12 @@ def load(path: str = LIB_PATH):
         "nne_cgemm_c64": (i32, [vp, i32, i32, i32, i32, i32, vp, vp, i32, C.c_longlong, vp, i32, C.c_longlong,
                                 vp, vp, i32, C.c_longlong, i32]),
         "nne_set_option": (None, [i32, i32]),
+        "nne_server_create": (i32, [i32, sz, i32, i32, i32, P(vp)]),
+        "nne_job_bytes": (sz, [P(JobStruct)]),
+        "nne_submit": (i32, [vp, P(JobStruct), P(C.c_uint64)]),
+        "nne_poll": (i32, [vp, C.c_uint64, i32, P(ResultStruct)]),
+        "nne_server_stats": (None, [vp, P(i32), P(i32), P(i32), P(sz)]),
+        "nne_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -282,7 +308,7 @@ class State:
 
 
 PROF_CLASSES = ("gemm", "superop_epilogue", "tridiag", "bisect", "inviter", "backtransform", "qr_factor",
-                "wy_apply", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit")
+                "wy_apply", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit", "gemm_tc")
 
 
 def kernel_launches() -> int:
@@ -300,3 +326,99 @@ def prof_collect():
     wk = np.zeros(16)
     load().nne_prof_collect(_hptr(ms), _hptr(cnt), _hptr(wk), 16)
     return {name: (float(ms[i]), int(cnt[i]), float(wk[i])) for i, name in enumerate(PROF_CLASSES)}
+
+
+class Job:
+    """Host arrays of one nne_job, kept alive while the struct points at them.
+
+    layers: sequence of (left_qubits, U (g,4,4) complex128, direction) in
+    application order; rates (n_lambda, 4) channel strengths per level."""
+
+    def __init__(self, n: int, layers, lambdas, rates, chi: int, paulis, dtype: int = C64,
+                 trunc: int = TRUNC_EXACT, sketch: Optional[np.ndarray] = None, power_iters: int = 1,
+                 bits=None, fit_method: int = FIT_EXP_LOGLIN, fit_degree: int = 2, lambda_star: float = 1.0):
+        self.n, self.chi = n, chi
+        self.layer_gates = np.array([len(qs) for qs, _, _ in layers], dtype=np.int32)
+        self.layer_dir = np.array([d for _, _, d in layers], dtype=np.int32)
+        self.left = np.ascontiguousarray(np.concatenate([np.asarray(qs, np.int32) for qs, _, _ in layers])
+                                         if layers else np.zeros(0, np.int32))
+        self.U = np.ascontiguousarray(np.concatenate([np.asarray(us, np.complex128).reshape(-1, 4, 4)
+                                                      for _, us, _ in layers]) if layers
+                                      else np.zeros((0, 4, 4), np.complex128))
+        self.lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
+        self.rates = np.ascontiguousarray(rates, dtype=np.float64).reshape(-1, 4)
+        self.paulis = np.ascontiguousarray(paulis, dtype=np.uint8).reshape(-1, n)
+        self.bits = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)
+        self.sketch = None if sketch is None else np.ascontiguousarray(sketch)
+        self.n_lambda, self.n_obs = len(self.lambdas), self.paulis.shape[0]
+        s = JobStruct()
+        s.n_qubits, s.n_layers = n, len(self.layer_gates)
+        s.layer_gates, s.layer_dir = _hptr(self.layer_gates), _hptr(self.layer_dir)
+        s.left_qubit, s.U = _hptr(self.left), _hptr(self.U)
+        s.n_lambda, s.lambdas, s.rates = self.n_lambda, _hptr(self.lambdas), _hptr(self.rates)
+        s.chi, s.dtype, s.trunc = chi, dtype, trunc
+        if self.sketch is not None:
+            s.sketch, s.sketch_rows, s.sketch_cols = _hptr(self.sketch), self.sketch.shape[0], self.sketch.shape[1]
+            s.power_iters = power_iters
+        s.init_bits = _hptr(self.bits)
+        s.n_obs, s.paulis = self.n_obs, _hptr(self.paulis)
+        s.fit_method, s.fit_degree, s.lambda_star = fit_method, fit_degree, lambda_star
+        self.struct = s
+        self.gate_steps = int(self.layer_gates.sum()) * self.n_lambda
+
+    def bytes(self) -> int:
+        return int(load().nne_job_bytes(C.byref(self.struct)))
+
+
+class Server:
+    """nne_server: worker threads running whole jobs on the GPU (FIFO admission
+    under a device-memory budget).  dry_run: queueing only, no GPU work."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, workers: int = 2, dry_run: bool = False,
+                 dry_run_us: int = 0):
+        L = load()
+        h = C.c_void_p()
+        _check(L.nne_server_create(device, hbm_budget_bytes, workers, SERVER_DRYRUN if dry_run else 0,
+                                   dry_run_us, C.byref(h)))
+        self.h = h
+        self.jobs = {}
+
+    def close(self):
+        if self.h:
+            load().nne_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, job: Job) -> int:
+        t = C.c_uint64()
+        _check(load().nne_submit(self.h, C.byref(job.struct), C.byref(t)))
+        self.jobs[t.value] = job
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """None while pending, else a dict with the job's status and results."""
+        job = self.jobs[ticket]
+        vals = np.zeros((job.n_lambda, job.n_obs))
+        lf = np.zeros(job.n_lambda)
+        est = np.zeros(job.n_obs)
+        fst = np.zeros(job.n_obs, dtype=np.int32)
+        r = ResultStruct()
+        r.values, r.log_fid, r.estimate, r.fit_status = _hptr(vals), _hptr(lf), _hptr(est), _hptr(fst)
+        rc = load().nne_poll(self.h, ticket, timeout_ms, C.byref(r))
+        if rc == PENDING:
+            return None
+        _check(rc)
+        del self.jobs[ticket]
+        return {"status": r.status, "error": r.error.decode(errors="replace"), "values": vals, "log_fid": lf,
+                "estimate": est, "fit_status": fst, "t_submit": r.t_submit, "t_start": r.t_start,
+                "t_end": r.t_end, "gate_steps": r.gate_steps, "bytes": r.bytes_reserved}
+
+    def stats(self):
+        q, ru, d, b = C.c_int(), C.c_int(), C.c_int(), C.c_size_t()
+        load().nne_server_stats(self.h, C.byref(q), C.byref(ru), C.byref(d), C.byref(b))
+        return {"queued": q.value, "running": ru.value, "done": d.value, "bytes_reserved": b.value}

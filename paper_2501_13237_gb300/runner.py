@@ -46,3 +46,20 @@ def emulate(ctx: nne.Context, circuit, rates: np.ndarray, chi: int, paulis: np.n
     evolve(st, layers if layers is not None else build_layer_superops(ctx, circuit, rates))
     vals, lf = st.expect(paulis)
     return st, vals, lf
+
+
+FIT_CODES = {"exp": nne.FIT_EXP_LOGLIN, "exp3": nne.FIT_EXP3, "poly2": nne.FIT_POLY, "poly1": nne.FIT_POLY}
+
+
+def job_for(w, chi=None, dtype: int = nne.C64, trunc: int = nne.TRUNC_EXACT, sketch=None, power_iters: int = 1,
+            paulis=None) -> nne.Job:
+    """A server job (nne_job) for a workload: its circuit in the snake schedule,
+    one level per lambda, its observables and fit."""
+    from workloads import pauli_codes
+    fit = FIT_CODES.get(w.fit, nne.FIT_EXP_LOGLIN)
+    degree = int(w.fit[4:]) if w.fit.startswith("poly") else 2
+    return nne.Job(w.n, layer_plan(w.circuit), np.asarray(w.lambdas), w.rate_table(),
+                   w.chi if chi is None else chi,
+                   pauli_codes(w.observables, w.n) if paulis is None else paulis,
+                   dtype=dtype, trunc=trunc, sketch=sketch, power_iters=power_iters, bits=w.bits(),
+                   fit_method=fit, fit_degree=degree, lambda_star=w.lambda_star)

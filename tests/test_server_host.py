@@ -1,0 +1,105 @@
+"""Host logic of the serving loop (nne_submit / nne_poll) on the CPU: the
+server's dry-run mode runs no GPU work, so queueing, FIFO admission under a
+device-memory budget, ticket handling and argument checks are tested here."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from paper_2501_13237_gb300 import nne, runner
+
+
+def _job(n=8, depth=4, chi=16, seed=0, lambdas=(1.0, 2.0)):
+    w = wl.Workload("t", wl.brickwork_circuit(n, depth, seed), wl.NoiseModel(depol2=1e-3),
+                    tuple(lambdas), chi, wl.obs_z(n), 1.0, "exp")
+    return runner.job_for(w)
+
+
+def test_job_bytes_monotone():
+    small = _job(chi=16).bytes()
+    assert small > 0
+    assert _job(chi=64).bytes() > small
+    assert _job(chi=16, lambdas=(1.0, 2.0, 3.0, 4.0)).bytes() > small
+    # the bond capacity saturates at 4^(n/2): chi beyond it changes nothing
+    assert _job(n=4, chi=16).bytes() == _job(n=4, chi=64).bytes()
+
+
+def test_fifo_admission_under_budget():
+    job = _job()
+    b = job.bytes()
+    srv = nne.Server(hbm_budget_bytes=2 * b + b // 2, workers=4, dry_run=True, dry_run_us=60000)
+    tickets = [srv.submit(_job(seed=i)) for i in range(6)]
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    assert all(r["status"] == -7 for r in res)            # dry run: no values
+    assert all(r["bytes"] == b for r in res)
+    starts = [r["t_start"] for r in res]
+    assert starts == sorted(starts)                       # admitted in submission order
+    # never more than two jobs inside the budget at once
+    for r in res:
+        mid = 0.5 * (r["t_start"] + r["t_end"])
+        overlap = sum(1 for q in res if q["t_start"] <= mid < q["t_end"])
+        assert overlap <= 2
+    # with four workers and room for two, the six jobs take three rounds
+    assert res[-1]["t_end"] - res[0]["t_start"] >= 3 * 0.06 * 0.9
+
+
+def test_unlimited_budget_runs_workers_in_parallel():
+    srv = nne.Server(hbm_budget_bytes=0, workers=3, dry_run=True, dry_run_us=80000)
+    tickets = [srv.submit(_job(seed=i)) for i in range(3)]
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    assert max(r["t_start"] for r in res) < min(r["t_end"] for r in res)
+
+
+def test_poll_pending_and_unknown_ticket():
+    srv = nne.Server(workers=1, dry_run=True, dry_run_us=200000)
+    t = srv.submit(_job())
+    assert srv.poll(t, timeout_ms=0) is None
+    st = srv.stats()
+    assert st["queued"] + st["running"] == 1
+    r = srv.poll(t, timeout_ms=-1)
+    assert r is not None and r["t_end"] >= r["t_start"] >= r["t_submit"]
+    srv.jobs[12345] = srv.jobs.get(t, _job())
+    with pytest.raises(nne.NNEError) as e:
+        srv.poll(12345, timeout_ms=0)
+    assert e.value.status == -1
+    srv.close()
+
+
+def test_oversize_job_refused():
+    job = _job(chi=64)
+    srv = nne.Server(hbm_budget_bytes=job.bytes() - 1, workers=1, dry_run=True)
+    with pytest.raises(nne.NNEError) as e:
+        srv.submit(job)
+    assert e.value.status == -2
+    srv.close()
+
+
+@pytest.mark.parametrize("field,value", [("paulis", 5), ("rates", 2.0), ("left", 7), ("dir", 0)])
+def test_bad_job_rejected(field, value):
+    job = _job()
+    if field == "paulis":
+        job.paulis[0, 0] = value
+    elif field == "rates":
+        job.rates[0, 1] = value
+    elif field == "left":
+        job.left[0] = value
+    else:
+        job.layer_dir[0] = value
+    srv = nne.Server(workers=1, dry_run=True)
+    with pytest.raises(nne.NNEError) as e:
+        srv.submit(job)
+    assert e.value.status == -1
+    srv.close()
+
+
+def test_destroy_drops_queued_jobs():
+    srv = nne.Server(workers=1, dry_run=True, dry_run_us=100000)
+    for i in range(4):
+        srv.submit(_job(seed=i))
+    time.sleep(0.02)
+    t0 = time.time()
+    srv.close()                      # finishes the running job only
+    assert time.time() - t0 < 0.35
