@@ -36,6 +36,9 @@ template <typename R> __host__ __device__ __forceinline__ void fmac_(cx<R>& a, c
 template <typename R> __device__ __forceinline__ cx<R> shfl_xor(cx<R> v, int m) {
   return mk(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
 }
+template <typename R> __device__ __forceinline__ cx<R> shfl_idx(cx<R> v, int src) {
+  return mk(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
 template <typename R> __device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
   for (int m = 16; m > 0; m >>= 1) v = v + shfl_xor(v, m);
   return v;

@@ -257,6 +257,325 @@ __global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(cx<R>* Ab, long lo
     for (int e = tid; e < QB * QB; e += QR_THREADS) T[e] = Ts[e / QB][e % QB];
 }
 
+// Shared-memory state of one register-resident panel factorisation.  Norm
+// sums are kept in the state's precision R: the downdate below cancels at
+// most half of a norm before an exact recompute, which bounds its relative
+// error at a few units of R.
+template <typename R>
+struct PanelMsg {
+  cx<R> w[QB];   // c < j: v_c^H v_j ; c > j: v_j^H a_c (partials over own rows)
+  cx<R> ex[3];   // a_j[j+1] (owner of row j), v_{j+1} and a_{j+1}[j+1] (owner of row j+1); 0 elsewhere
+  R nrm;         // partial squared norm of the next pivot column
+};
+template <typename R>
+struct PanelShared {
+  PanelMsg<R> msg[2][QR_CS_MAX];
+  cx<R> red[QR_WARPS][QB];
+  R redn[QR_WARPS];
+  cx<R> wfull[QB];
+  cx<R> gcol[QB];
+  cx<R> alphas[QB];
+  cx<R> Ts[QB][QB + 1];
+  cx<R> ex_loc[3];
+  cx<R> ex_s[3];
+  R nrm_s;
+  cx<R> x0_s;
+  R xn2_s;
+  int recompute_s;
+  cx<R> alpha_s;
+  R inv_s, tau_s;
+};
+
+// Reflector pivot from the squared norm xn2 of the column at and below the
+// diagonal and its diagonal entry x0: alpha = -e^{i arg x0} ||x||,
+// un = ||x - alpha e_0||, tau = 2 (0 for a zero column).  Evaluated in R.
+template <typename R>
+__device__ __forceinline__ void hh_pivot(R xn2, cx<R> x0, cx<R>* alpha, R* inv, R* tau) {
+  const R ax0 = sqrt(norm2(x0)), xn = sqrt(xn2);
+  cx<R> a = mk<R>(0, 0);
+  R un = 0;
+  if (xn > R(0)) {
+    const R pr = ax0 > R(0) ? x0.re / ax0 : R(1), pi = ax0 > R(0) ? x0.im / ax0 : R(0);
+    a = mk<R>(-xn * pr, -xn * pi);
+    un = sqrt(R(2) * xn2 + R(2) * xn * ax0);
+  }
+  *alpha = a;
+  *inv = un > R(0) ? R(1) / un : R(0);
+  *tau = un > R(0) ? R(2) : R(0);
+}
+
+// One cluster round: the squared norm of a column over the panel rows from
+// a given row down (sacc: this thread's partial, meaningful on lane c), and
+// with with_x0 the column's diagonal entry (x0_mine, held by the thread
+// holds_x0); tid 0 then forms the reflector pivot.
+template <typename R>
+__device__ __forceinline__ void panel_norm_round(R sacc, cx<R> x0_mine, bool holds_x0, PanelShared<R>& sh,
+                                                 cg::cluster_group& cluster, int CS, int rank, int c, bool with_x0,
+                                                 bool x0_here, int& round) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (lane == c) sh.redn[wid] = sacc;
+  if (with_x0 && holds_x0) sh.ex_loc[2] = x0_mine;
+  __syncthreads();
+  const int buf = round & 1;
+  if (tid < CS) {
+    R t0 = 0, t1 = 0;
+    for (int w = 0; w < QR_WARPS; w += 2) {
+      t0 += sh.redn[w];
+      t1 += sh.redn[w + 1];
+    }
+    PanelMsg<R>* dst = cluster.map_shared_rank(&sh.msg[buf][rank], tid);
+    dst->nrm = t0 + t1;
+    dst->ex[2] = (with_x0 && x0_here) ? sh.ex_loc[2] : mk<R>(0, 0);
+  }
+  cluster.sync();
+  if (tid == 0) {
+    R t = 0;
+    cx<R> x0 = mk<R>(0, 0);
+    for (int src = 0; src < CS; ++src) {
+      t += sh.msg[buf][src].nrm;
+      x0 = x0 + sh.msg[buf][src].ex[2];
+    }
+    sh.xn2_s = t;
+    if (with_x0) sh.x0_s = x0;
+    cx<R> al;
+    R iv, ta;
+    hh_pivot<R>(sh.xn2_s, sh.x0_s, &al, &iv, &ta);
+    sh.alpha_s = al;
+    sh.inv_s = iv;
+    sh.tau_s = ta;
+  }
+  ++round;
+  __syncthreads();
+}
+
+// Register-resident panel factorisation (same arithmetic per column as a
+// plain Householder QR): warp w of a CTA holds its local rows w, w + 16, ...
+// (at most RPW of them), lane c holds column c, so the reflector entry of a
+// row is a shuffle from lane j and no shared-memory traffic touches the
+// panel.  Rows are dealt to the CTAs of the cluster cyclically.  Column j
+// takes one cluster round: every CTA pushes its partial sums into every
+// CTA's shared memory, then all sum them in rank order.  The squared norm of
+// column j+1 below row j is downdated in the same round (the reflector is
+// unitary on rows >= j); when that cancels more than half of it an extra
+// round recomputes it.  T is built column by column from the v_c^H v_j of
+// the same rounds.
+template <typename R, int RPW>
+__global__ void __launch_bounds__(QR_THREADS) qr_panel_reg_kernel(cx<R>* Ab, long long sA, int lda, int m, int pb,
+                                                                   int bw, cx<R>* Vb, long long sV, int ldv,
+                                                                   cx<R>* Tb, long long sT) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int z = blockIdx.y;
+  cx<R>* A = Ab + z * sA;
+  cx<R>* V = Vb + z * sV;
+  cx<R>* T = Tb + z * sT;
+  __shared__ PanelShared<R> sh;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int mp = m - pb;
+  const int nloc = mp > rank ? (mp - rank + CS - 1) / CS : 0;
+  // this warp's live registers: k < kmax (local row wid + 16 k < nloc)
+  const int kmax = nloc > wid ? (nloc - wid + QR_WARPS - 1) / QR_WARPS : 0;
+  cx<R> a[RPW];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int li = wid + QR_WARPS * k;
+    a[k] = mk<R>(0, 0);
+    if (li < nloc && lane < bw) a[k] = A[(long long)(pb + rank + li * CS) * lda + pb + lane];
+  }
+  for (int e = tid; e < QB * QB; e += QR_THREADS) sh.Ts[e / QB][e % QB] = mk<R>(0, 0);
+  // every CTA of the cluster is running before anyone writes into its shared memory
+  cluster.sync();
+  int round = 0;
+  {
+    // column 0 over all rows, and its entry in row 0 (rank 0, warp 0, register 0, lane 0)
+    R sacc = 0;
+#pragma unroll
+    for (int k = 0; k < RPW; ++k)
+      if (k < kmax) sacc += norm2(a[k]);
+    panel_norm_round<R>(sacc, a[0], rank == 0 && wid == 0 && lane == 0, sh, cluster, CS, rank, 0, true, rank == 0,
+                        round);
+  }
+  for (int j = 0; j < bw; ++j) {
+    const cx<R> x0 = sh.x0_s;
+    const cx<R> alpha = sh.alpha_s;
+    const R inv = sh.inv_s, tau = sh.tau_s;
+    if (tid == 0) sh.alphas[j] = alpha;
+    const int owner = j % CS;
+    const bool has_next = j + 1 < bw;
+    // registers k >= kmin of this warp hold rows >= j: local row li >= first local row >= j
+    const int l0 = j > rank ? (j - rank + CS - 1) / CS : 0;
+    const int kmin = l0 > wid ? (l0 - wid + QR_WARPS - 1) / QR_WARPS : 0;
+    // row of register k: rank + (wid + 16 k) CS; rows j and j+1, if here, sit at these registers
+    const int dj = j - rank - wid * CS, dj1 = j + 1 - rank - wid * CS;
+    const int kj = (dj >= 0 && dj % (QR_WARPS * CS) == 0) ? dj / (QR_WARPS * CS) : -1;
+    const int kj1 = (dj1 >= 0 && dj1 % (QR_WARPS * CS) == 0 && j + 1 < mp) ? dj1 / (QR_WARPS * CS) : -1;
+    // v = (x - alpha e_j) / un (every lane forms it from lane j's entry; lane j keeps it);
+    // partials: lane c < j: v_c^H v_j; lane c > j: v_j^H a_c; lane j+1 also |a_{j+1}|^2;
+    // and the pre-update entries every CTA needs for the next pivot
+    // branch-free: every lane accumulates conj(x) v; lanes c > j want v^H a_c = conj of that
+    cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+    R nacc = 0;
+    cx<R> e_a = mk<R>(0, 0), e_b = mk<R>(0, 0);
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+      if (k >= kmin && k < kmax) {
+        cx<R> u = shfl_idx(a[k], j);
+        if (k == kj) u = u - alpha;
+        const cx<R> v = inv * u;
+        if (lane == j) a[k] = v;
+        const cx<R> x = a[k];
+        if (k & 1) fmac_(acc1, x, v); else fmac_(acc0, x, v);
+        nacc += norm2(x);
+        if (k == kj) e_a = x;                       // row j: lane j+1 holds a_j[j+1]
+        if (k == kj1) e_b = lane == j ? v : x;      // row j+1: lane j -> v_{j+1}, lane j+1 -> a_{j+1}[j+1]
+      }
+    }
+    {
+      const cx<R> acc = acc0 + acc1;
+      sh.red[wid][lane] = lane > j ? conj(acc) : acc;
+    }
+    if (lane == j + 1) sh.redn[wid] = nacc;
+    if (has_next) {
+      if (kj >= 0 && lane == j + 1) sh.ex_loc[0] = e_a;
+      if (kj1 >= 0 && lane == j) sh.ex_loc[1] = e_b;
+      if (kj1 >= 0 && lane == j + 1) sh.ex_loc[2] = e_b;
+    }
+    __syncthreads();
+    const int buf = round & 1;
+    if (tid < QB) {
+      cx<R> t0 = mk<R>(0, 0), t1 = t0, t2 = t0, t3 = t0;
+      for (int w = 0; w < QR_WARPS; w += 4) {
+        t0 = t0 + sh.red[w][tid];
+        t1 = t1 + sh.red[w + 1][tid];
+        t2 = t2 + sh.red[w + 2][tid];
+        t3 = t3 + sh.red[w + 3][tid];
+      }
+      const cx<R> t = (t0 + t1) + (t2 + t3);
+      for (int d = 0; d < CS; ++d) cluster.map_shared_rank(&sh.msg[buf][rank], d)->w[tid] = t;
+    } else if (tid == QB) {
+      R nt = 0;
+      cx<R> e0 = mk<R>(0, 0), e1 = mk<R>(0, 0), e2 = mk<R>(0, 0);
+      if (has_next) {
+        R n0 = 0, n1 = 0;
+        for (int w = 0; w < QR_WARPS; w += 2) {
+          n0 += sh.redn[w];
+          n1 += sh.redn[w + 1];
+        }
+        nt = n0 + n1;
+        if (rank == owner) e0 = sh.ex_loc[0];
+        if (j + 1 < mp && rank == (j + 1) % CS) {
+          e1 = sh.ex_loc[1];
+          e2 = sh.ex_loc[2];
+        }
+      }
+      for (int d = 0; d < CS; ++d) {
+        PanelMsg<R>* dst = cluster.map_shared_rank(&sh.msg[buf][rank], d);
+        dst->ex[0] = e0;
+        dst->ex[1] = e1;
+        dst->ex[2] = e2;
+        dst->nrm = nt;
+      }
+    }
+    cluster.sync();
+    ++round;
+    if (tid < QB) {
+      cx<R> t0 = mk<R>(0, 0), t1 = t0;
+      int src = 0;
+      for (; src + 1 < CS; src += 2) {
+        t0 = t0 + sh.msg[buf][src].w[tid];
+        t1 = t1 + sh.msg[buf][src + 1].w[tid];
+      }
+      if (src < CS) t0 = t0 + sh.msg[buf][src].w[tid];
+      const cx<R> t = t0 + t1;
+      sh.wfull[tid] = tid > j ? mk<R>(2 * t.re, 2 * t.im) : mk<R>(0, 0);
+      sh.gcol[tid] = tid < j ? t : mk<R>(0, 0);
+    } else if (tid == QB) {
+      R nt = 0;
+      cx<R> e0 = mk<R>(0, 0), e1 = mk<R>(0, 0), e2 = mk<R>(0, 0);
+      for (int src = 0; src < CS; ++src) {
+        nt += sh.msg[buf][src].nrm;
+        e0 = e0 + sh.msg[buf][src].ex[0];
+        e1 = e1 + sh.msg[buf][src].ex[1];
+        e2 = e2 + sh.msg[buf][src].ex[2];
+      }
+      sh.nrm_s = nt;
+      sh.ex_s[0] = e0;
+      sh.ex_s[1] = e1;
+      sh.ex_s[2] = e2;
+    }
+    __syncthreads();
+    // T[0:j, j] = -tau_j T[0:j, 0:j] (V^H v_j), T[j][j] = tau_j (rank 0, last warp)
+    if (rank == 0 && wid == QR_WARPS - 1) {
+      cx<R> ta0 = mk<R>(0, 0), ta1 = ta0;
+      if (lane < j) {
+        int l = lane;
+        for (; l + 1 < j; l += 2) {
+          fma_(ta0, sh.Ts[lane][l], sh.gcol[l]);
+          fma_(ta1, sh.Ts[lane][l + 1], sh.gcol[l + 1]);
+        }
+        if (l < j) fma_(ta0, sh.Ts[lane][l], sh.gcol[l]);
+        const cx<R> ta = ta0 + ta1;
+        sh.Ts[lane][j] = mk<R>(-tau * ta.re, -tau * ta.im);
+      }
+      if (lane == j) sh.Ts[j][j] = mk<R>(tau, 0);
+    }
+    // a_c <- a_c - v (2 v^H a_c), c in (j, bw), own rows >= j
+    if (has_next) {
+      const cx<R> wf = sh.wfull[lane];
+      const bool upd = lane > j && lane < bw;
+#pragma unroll
+      for (int k = 0; k < RPW; ++k)
+        if (k >= kmin && k < kmax) {
+          const cx<R> v = shfl_idx(a[k], j);
+          if (upd) a[k] = hh_upd(a[k], v, wf);
+        }
+    }
+    if (tid == 0 && has_next) {
+      const cx<R> vj = inv * (x0 - alpha);                      // the owner's v_j, same operations
+      const cx<R> ajn = hh_upd(sh.ex_s[0], vj, sh.wfull[j + 1]);      // a'_j[j+1]
+      const cx<R> x0n = j + 1 < mp ? hh_upd(sh.ex_s[2], sh.ex_s[1], sh.wfull[j + 1]) : mk<R>(0, 0);
+      const R nA = sh.nrm_s;
+      const R xn2n = nA - norm2(ajn);
+      sh.x0_s = x0n;
+      sh.xn2_s = xn2n > R(0) ? xn2n : R(0);
+      sh.recompute_s = !(xn2n > R(0.5) * nA);
+      if (!sh.recompute_s) {
+        cx<R> al;
+        R iv, ta;
+        hh_pivot<R>(sh.xn2_s, x0n, &al, &iv, &ta);
+        sh.alpha_s = al;
+        sh.inv_s = iv;
+        sh.tau_s = ta;
+      }
+    }
+    __syncthreads();
+    if (has_next && sh.recompute_s) {
+      // column j+1 over rows >= j+1
+      const int l1 = j + 1 > rank ? (j + 1 - rank + CS - 1) / CS : 0;
+      const int kmin1 = l1 > wid ? (l1 - wid + QR_WARPS - 1) / QR_WARPS : 0;
+      R sacc = 0;
+#pragma unroll
+      for (int k = 0; k < RPW; ++k)
+        if (k >= kmin1 && k < kmax) sacc += norm2(a[k]);
+      panel_norm_round<R>(sacc, mk<R>(0, 0), false, sh, cluster, CS, rank, j + 1, false, false, round);
+    }
+  }
+  // write back V and the R part of A
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int li = wid + QR_WARPS * k;
+    if (li < nloc && lane < bw) {
+      const int pi = rank + li * CS;
+      const long long gi = pb + pi;
+      V[gi * ldv + pb + lane] = pi >= lane ? a[k] : mk<R>(0, 0);
+      A[gi * lda + pb + lane] = pi < lane ? a[k] : (pi == lane ? sh.alphas[lane] : mk<R>(0, 0));
+    }
+  }
+  if (rank == 0)
+    for (int e = tid; e < QB * QB; e += QR_THREADS) T[e] = sh.Ts[e / QB][e % QB];
+}
+
 template <typename R>
 __global__ void qr_extract_r2_kernel(const cx<R>* Ab, long long sA, int lda, int k, int n, cx<R>* Rb, long long sR) {
   const int z = blockIdx.y;
@@ -326,8 +645,24 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
       double work = 0;
       for (int j = 0; j < bw; ++j) work += 8.0 * (double)(mp - j) * (2.0 * (bw - 1 - j) + j + 1);
       ProfScope ps(st, K_QR_FACTOR, 1, work * batch);
-      e = launch_cluster_qr(qr_panel_kernel<R>, cs, batch, smem, st, A, sA, n, m, pb, bw, V, sV, n, T + p * QB * QB,
-                            sT, maxloc);
+      // register-resident panel when every CTA's rows fit 16 warps x 16 registers
+      int csr = mp >= 512 ? 8 : (mp >= 128 ? 4 : (mp >= 32 ? 2 : 1));
+      if ((mp + csr - 1) / csr > 16 * QR_WARPS) csr = 16;
+      const int nl = (mp + csr - 1) / csr;
+      cx<R>* Tp = T + p * QB * QB;
+      if (nl <= 1 * QR_WARPS)
+        e = launch_cluster_qr(qr_panel_reg_kernel<R, 1>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
+      else if (nl <= 2 * QR_WARPS)
+        e = launch_cluster_qr(qr_panel_reg_kernel<R, 2>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
+      else if (nl <= 4 * QR_WARPS)
+        e = launch_cluster_qr(qr_panel_reg_kernel<R, 4>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
+      else if (nl <= 8 * QR_WARPS)
+        e = launch_cluster_qr(qr_panel_reg_kernel<R, 8>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
+      else if (nl <= 16 * QR_WARPS)
+        e = launch_cluster_qr(qr_panel_reg_kernel<R, 16>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
+      else
+        e = launch_cluster_qr(qr_panel_kernel<R>, cs, batch, smem, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT,
+                              maxloc);
     }
     if (e != cudaSuccess) return e;
     const int nt = n - pb - bw;
