@@ -9,12 +9,68 @@
 // one thread per CTA), the products
 // p = A v are pushed to every CTA, and one more barrier closes the rank-2
 // update.  Reflector j is stored conjugated as row j of Vh (n x n).
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace nne {
 
+// Reflector of row r (the owner's own row, stored at Hl_row): x = conj of the
+// row's entries right of the diagonal (the column below it, by symmetry),
+// v = (x - alpha e_0) / ||x - alpha e_0||, alpha = -e^{i arg x_0} ||x||.
+// Writes v to vpub, conj(v) to row r of Vh, d[r] and e[r] = alpha.  Called by
+// every thread of the owning CTA; the norm is summed in R.
+template <typename R>
+__device__ __forceinline__ void tridiag_publish(const cx<R>* Hl_row, int n, int r, cx<R>* vpub, cx<R>* Vh, R* d,
+                                                cx<R>* e, R* red, cx<R>* alpha_s, R* inv_s) {
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+  const int m = n - r - 1;
+  R sp = 0;
+  for (int t = tid; t < m; t += nth) sp += norm2(Hl_row[r + 1 + t]);
+  sp = warp_sum_r(sp);
+  if (lane == 0) red[warp] = sp;
+  __syncthreads();
+  if (tid == 0) {
+    R xn2 = 0;
+    for (int w2 = 0; w2 < nw; ++w2) xn2 += red[w2];
+    const cx<R> x0 = conj(Hl_row[r + 1]);
+    const R ax0 = sqrt(norm2(x0)), xn = sqrt(xn2);
+    cx<R> alpha = mk<R>(0, 0);
+    R un = 0;
+    if (xn > R(0)) {
+      const R pr = ax0 > R(0) ? x0.re / ax0 : R(1), pi = ax0 > R(0) ? x0.im / ax0 : R(0);
+      alpha = mk<R>(-xn * pr, -xn * pi);
+      un = sqrt(R(2) * xn2 + R(2) * xn * ax0);
+    }
+    *alpha_s = alpha;
+    *inv_s = un > R(0) ? R(1) / un : R(0);
+    d[r] = Hl_row[r].re;
+    e[r] = alpha;
+  }
+  __syncthreads();
+  const cx<R> alpha = *alpha_s;
+  const R inv = *inv_s;
+  cx<R>* vr = Vh + (long long)r * n + (r + 1);
+  for (int t = tid; t < m; t += nth) {
+    cx<R> u = conj(Hl_row[r + 1 + t]);
+    if (t == 0) u = u - alpha;
+    const cx<R> v = inv * u;
+    vpub[t] = v;
+    vr[t] = conj(v);
+  }
+}
+
+// Householder tridiagonalisation of the Hermitian H[z] (n x n) by one
+// cluster.  Rows are dealt to the CTAs cyclically and stay in shared memory.
+// Column j: every CTA pulls v_j from the owner of row j, forms p = A v on
+// its rows and publishes p and its share of K = v^H p; after a cluster
+// barrier it pulls all of p and K, applies A <- A - v w^H - w v^H with
+// w = 2p - 2Kv to its rows, and the owner of row j+1 forms and publishes
+// v_{j+1}; a second barrier closes the column.  Sums run in a fixed order.
 template <typename R>
 __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long long sH, int n, R* db, cx<R>* eb,
                                                             int ldde, cx<R>* Vhb, long long sVh, int maxloc) {
@@ -28,12 +84,12 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
   cx<R>* Vh = Vhb + z * sVh;
   extern __shared__ unsigned char smem_raw[];
   cx<R>* Hl = reinterpret_cast<cx<R>*>(smem_raw);     // [maxloc][n] own rows
-  cx<R>* vbuf = Hl + (long long)maxloc * n;           // 2 x n: column j (pushed by its owner), double-buffered
-  cx<R>* w = vbuf + 2 * n;
-  cx<R>* p = w + n;
-  __shared__ double ks[2][16];                        // K partials pushed by every CTA
-  __shared__ R dpush[2];                              // diagonal entry pushed with the column
-  __shared__ double red[32];
+  cx<R>* vpub = Hl + (long long)maxloc * n;           // n: v published by the owner of the pivot row
+  cx<R>* vloc = vpub + n;                             // n: this CTA's copy of v
+  cx<R>* ppub = vloc + n;                             // n: p of own rows, at their offsets
+  cx<R>* w = ppub + n;                                // n: w = 2p - 2Kv
+  __shared__ R kpub;                                  // this CTA's share of K
+  __shared__ R red[32];
   __shared__ cx<R> alpha_s;
   __shared__ R inv_s, twoK_s;
   const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
@@ -42,61 +98,18 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
     const int li = (int)(e2 / n), c = (int)(e2 % n);
     Hl[e2] = H[(long long)(rank + li * CS) * n + c];
   }
-  // every CTA of the cluster is running before anyone writes into its shared memory
-  cluster.sync();
-  // column 0 below the diagonal = conj(row 0 tail), pushed by the owner of row 0
-  if (rank == 0) {
-    for (int t = tid; t + 1 < n; t += nth) {
-      const cx<R> x = conj(Hl[1 + t]);
-      for (int c = 0; c < CS; ++c) *cluster.map_shared_rank(vbuf + t, c) = x;
-    }
-    if (tid < CS) *cluster.map_shared_rank(&dpush[0], tid) = Hl[0].re;
-  }
+  __syncthreads();
+  if (n > 2 && rank == 0) tridiag_publish(Hl, n, 0, vpub, Vh, d, e, red, &alpha_s, &inv_s);
   cluster.sync();
   for (int j = 0; j + 2 < n; ++j) {
-    const int m = n - j - 1, owner = j % CS, buf = j & 1;
-    cx<R>* v = vbuf + buf * n;
-    const R djj = dpush[buf];
-    // Householder vector (every CTA, same arithmetic).  Squared norm: per-warp
-    // partials in R, combined in FP64 by one thread, which also forms alpha and
-    // 1/un (FP64 is slow on this part: keep it off the other threads).
+    const int m = n - j - 1, owner = j % CS;
+    // pull v_j
     {
-      R sp = 0;
-      for (int t = tid; t < m; t += nth) sp += norm2(v[t]);
-      sp = warp_sum_r(sp);
-      if (lane == 0) red[warp] = (double)sp;
+      const cx<R>* src = cluster.map_shared_rank(vpub, owner);
+      for (int t = tid; t < m; t += nth) vloc[t] = src[t];
     }
     __syncthreads();
-    if (tid == 0) {
-      double xn2 = 0;
-      for (int w2 = 0; w2 < nw; ++w2) xn2 += red[w2];
-      const cx<R> x0 = v[0];
-      const double ax0 = sqrt((double)norm2(x0)), xn = sqrt(xn2);
-      cx<R> alpha = mk<R>(0, 0);
-      double un = 0;
-      if (xn > 0) {
-        const double pr = ax0 > 0 ? (double)x0.re / ax0 : 1.0, pi = ax0 > 0 ? (double)x0.im / ax0 : 0.0;
-        alpha = mk<R>((R)(-xn * pr), (R)(-xn * pi));
-        un = sqrt(2.0 * xn2 + 2.0 * xn * ax0);
-      }
-      alpha_s = alpha;
-      inv_s = un > 0 ? (R)(1.0 / un) : R(0);
-      if (rank == owner) { d[j] = djj; e[j] = alpha; }
-    }
-    __syncthreads();
-    const cx<R> alpha = alpha_s;
-    const R inv = inv_s;
-    for (int t = tid; t < m; t += nth) {
-      cx<R> u = v[t];
-      if (t == 0) u = u - alpha;
-      v[t] = inv * u;
-    }
-    __syncthreads();
-    if (rank == owner) {
-      cx<R>* vr = Vh + (long long)j * n + (j + 1);
-      for (int t = tid; t < m; t += nth) vr[t] = conj(v[t]);
-    }
-    // p = A v on own rows i >= j+1, pushed to every CTA
+    // p = A v on own rows i > j; K share = sum Re(conj(v_t) p_t)
     const int lstart = (j + 1 - rank + CS - 1) / CS;
     R kp = 0;
     for (int li = lstart + warp; li < nloc; li += nw) {
@@ -105,57 +118,61 @@ __global__ void __launch_bounds__(256) tridiag_smem_kernel(const cx<R>* Hb, long
       cx<R> a0 = mk<R>(0, 0), a1 = a0, a2 = a0, a3 = a0;
       int k = lane;
       for (; k + 96 < m; k += 128) {
-        fma_(a0, row[k], v[k]);
-        fma_(a1, row[k + 32], v[k + 32]);
-        fma_(a2, row[k + 64], v[k + 64]);
-        fma_(a3, row[k + 96], v[k + 96]);
+        fma_(a0, row[k], vloc[k]);
+        fma_(a1, row[k + 32], vloc[k + 32]);
+        fma_(a2, row[k + 64], vloc[k + 64]);
+        fma_(a3, row[k + 96], vloc[k + 96]);
       }
-      for (; k < m; k += 32) fma_(a0, row[k], v[k]);
+      for (; k < m; k += 32) fma_(a0, row[k], vloc[k]);
       cx<R> acc = (a0 + a1) + (a2 + a3);
       acc = warp_sum(acc);
-      if (lane < CS) *cluster.map_shared_rank(p + t, lane) = acc;
-      if (lane == 0) kp += v[t].re * acc.re + v[t].im * acc.im;
+      if (lane == 0) {
+        ppub[t] = acc;
+        kp += vloc[t].re * acc.re + vloc[t].im * acc.im;
+      }
     }
-    if (lane == 0) red[warp] = (double)kp;
+    if (lane == 0) red[warp] = kp;
     __syncthreads();
-    if (tid < CS) {
-      double t = 0;
+    if (tid == 0) {
+      R t = 0;
       for (int w2 = 0; w2 < nw; ++w2) t += red[w2];
-      *cluster.map_shared_rank(&ks[buf][rank], tid) = t;
+      kpub = t;
     }
     cluster.sync();
-    if (tid == 0) {
-      double K = 0;
-      for (int c = 0; c < CS; ++c) K += ks[buf][c];
-      twoK_s = (R)(2.0 * K);
+    // pull p and K; w = 2p - 2Kv
+    if (warp == 0) {
+      R kk = lane < CS ? *cluster.map_shared_rank(&kpub, lane) : R(0);
+      for (int o = 1; o < 32; o <<= 1) {
+        const R other = __shfl_down_sync(0xffffffffu, kk, o);
+        kk += (lane + o < 32) ? other : R(0);
+      }
+      if (lane == 0) twoK_s = R(2) * kk;
     }
+    for (int t = tid; t < m; t += nth) w[t] = *cluster.map_shared_rank(ppub + t, (j + 1 + t) % CS);
     __syncthreads();
-    const R twoK = twoK_s;
-    for (int t = tid; t < m; t += nth) w[t] = mk<R>(2 * p[t].re - twoK * v[t].re, 2 * p[t].im - twoK * v[t].im);
+    {
+      const R twoK = twoK_s;
+      for (int t = tid; t < m; t += nth)
+        w[t] = mk<R>(2 * w[t].re - twoK * vloc[t].re, 2 * w[t].im - twoK * vloc[t].im);
+    }
     __syncthreads();
     for (int li = lstart + warp; li < nloc; li += nw) {
       const int i = rank + li * CS, t = i - j - 1;
       cx<R>* row = Hl + (long long)li * n + (j + 1);
-      const cx<R> vt = v[t], wt = w[t];
+      const cx<R> vt = vloc[t], wt = w[t];
 #pragma unroll 4
       for (int k = lane; k < m; k += 32) {
         cx<R> a = row[k];
-        const cx<R> wk = w[k], vk = v[k];
+        const cx<R> wk = w[k], vk = vloc[k];
         a.re -= vt.re * wk.re + vt.im * wk.im + wt.re * vk.re + wt.im * vk.im;
         a.im -= vt.im * wk.re - vt.re * wk.im + wt.im * vk.re - wt.re * vk.im;
         row[k] = a;
       }
     }
-    // the owner of row j+1 pushes its updated tail (the next column) and diagonal
+    // the owner of row j+1 forms and publishes the next reflector
     if (j + 3 < n && rank == (j + 1) % CS) {
       __syncthreads();
-      const cx<R>* rn = Hl + (long long)((j + 1) / CS) * n;
-      cx<R>* vn = vbuf + (buf ^ 1) * n;
-      for (int t = tid; t + j + 2 < n; t += nth) {
-        const cx<R> x = conj(rn[j + 2 + t]);
-        for (int c = 0; c < CS; ++c) *cluster.map_shared_rank(vn + t, c) = x;
-      }
-      if (tid < CS) *cluster.map_shared_rank(&dpush[buf ^ 1], tid) = rn[j + 1].re;
+      tridiag_publish(Hl + (long long)((j + 1) / CS) * n, n, j + 1, vpub, Vh, d, e, red, &alpha_s, &inv_s);
     }
     cluster.sync();
   }
@@ -248,26 +265,80 @@ static cudaError_t launch_cl(K kernel, int cs, int batch, size_t smem, cudaStrea
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-constexpr size_t SMEM_LIMIT = 220 * 1024;
+constexpr size_t SMEM_LIMIT = 224 * 1024;   // dynamic shared memory per CTA (227 KB less the static part)
 
-// Cluster size whose shared memory holds the matrix, or 0 if none does.
+template <typename R>
+static size_t tridiag_smem_bytes(int n, int cs) {
+  const size_t maxloc = (n + cs - 1) / cs;
+  return sizeof(cx<R>) * (maxloc * n + 4 * (size_t)n);
+}
+
+// Smallest power-of-two cluster whose shared memory holds the matrix (0: none does).
 template <typename R>
 int smem_cluster_size(int n) {
   for (int cs = 1; cs <= 16; cs *= 2) {
     const size_t maxloc = (n + cs - 1) / cs;
-    const size_t bytes = sizeof(cx<R>) * (maxloc * n + 4 * (size_t)n);
-    if (bytes <= SMEM_LIMIT && (cs >= 16 || maxloc <= 64)) return cs;
+    if (tridiag_smem_bytes<R>(n, cs) <= SMEM_LIMIT && (cs >= 16 || maxloc <= 64)) return cs;
   }
   return 0;
+}
+
+// Cluster size for `batch` matrices: among the sizes from smem_cluster_size(n)
+// up to 16 that hold the matrix, the largest whose clusters all fit on the GPU
+// at once (cudaOccupancyMaxActiveClusters); a cluster of 16 does not fit on
+// every GPC, so for a batch of 8 a size of 13 or 14 can finish in one wave
+// where 16 needs two.  Cached per (n, batch) and device.
+template <typename R>
+static int tridiag_cluster_size(int n, int batch, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(n, batch, dev);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  const int cs0 = smem_cluster_size<R>(n);
+  int best = cs0, best_waves = 1 << 30;
+  for (int cs = std::max(cs0, 2); cs <= 16 && cs0 > 0; ++cs) {
+    const size_t smem = tridiag_smem_bytes<R>(n, cs);
+    if (smem > SMEM_LIMIT) continue;
+    if (ensure_kernel_smem((const void*)tridiag_smem_kernel<R>, smem, cs > 8) != cudaSuccess) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, batch, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, (const void*)tridiag_smem_kernel<R>, &cfg) != cudaSuccess ||
+        active < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const int waves = (batch + active - 1) / active;
+    if (waves < best_waves || (waves == best_waves && cs > best)) {
+      best_waves = waves;
+      best = cs;
+    }
+  }
+  cache[key] = best;
+  return best;
 }
 
 template <typename R>
 cudaError_t tridiag_smem(cudaStream_t st, const cx<R>* H, long long sH, int n, R* d, cx<R>* e, int ldde, cx<R>* Vh,
                          long long sVh, int batch) {
-  const int cs = smem_cluster_size<R>(n);
-  if (cs == 0) return cudaErrorInvalidValue;
+  if (smem_cluster_size<R>(n) == 0) return cudaErrorInvalidValue;
+  const int cs = tridiag_cluster_size<R>(n, batch, st);
   const int maxloc = (n + cs - 1) / cs;
-  const size_t smem = sizeof(cx<R>) * ((size_t)maxloc * n + 4 * (size_t)n);
+  const size_t smem = tridiag_smem_bytes<R>(n, cs);
   ProfScope ps(st, K_TRIDIAG, 1, 16.0 / 3.0 * (double)n * n * n * batch);   // Hermitian tridiagonalisation flops
   return launch_cl(tridiag_smem_kernel<R>, cs, batch, smem, st, H, sH, n, d, e, ldde, Vh, sVh, maxloc);
 }
