@@ -132,7 +132,7 @@ template <int OPA, int OPB>
 __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, float2 alpha, const float2* __restrict__ A,
                                                           long long sA, int lda, const float2* __restrict__ B,
                                                           long long sB, int ldb, float2 beta, float2* __restrict__ C,
-                                                          long long sC, int ldc, int* err) {
+                                                          long long sC, int ldc, int ksplit, int kc, int* err) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -140,12 +140,14 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int z = blockIdx.z;
+  // grid z = matrix x K-slice; slice s covers k in [kbeg, kend) and writes its own C block
+  const int zz = blockIdx.z, z = zz / ksplit, slice = zz % ksplit;
+  const int kbeg = slice * kc, kend = min(K, kbeg + kc);
   A += z * sA;
   B += z * sB;
-  C += z * sC;
+  C += zz * sC;
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  const int nchunks = (K + BKC - 1) / BKC;
+  const int nchunks = kend > kbeg ? (kend - kbeg + BKC - 1) / BKC : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -172,17 +174,17 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
     const int t = threadIdx.x;
     float2 va[BKC], vb[BKC];
     auto load_chunk = [&](int c) {
-      const int k0 = c * BKC;
+      const int k0 = kbeg + c * BKC;
       const int i = row0 + t, j = col0 + t;
       if (OPA == OP_N) {
         const float2* src = A + (long long)i * lda + k0;
 #pragma unroll
-        for (int kk = 0; kk < BKC; ++kk) va[kk] = (i < M && k0 + kk < K) ? src[kk] : make_float2(0.f, 0.f);
+        for (int kk = 0; kk < BKC; ++kk) va[kk] = (i < M && k0 + kk < kend) ? src[kk] : make_float2(0.f, 0.f);
       } else {
 #pragma unroll
         for (int kk = 0; kk < BKC; ++kk) {
           const int k = k0 + kk;
-          float2 v = (i < M && k < K) ? A[(long long)k * lda + i] : make_float2(0.f, 0.f);
+          float2 v = (i < M && k < kend) ? A[(long long)k * lda + i] : make_float2(0.f, 0.f);
           v.y = -v.y;
           va[kk] = v;
         }
@@ -191,13 +193,13 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
 #pragma unroll
         for (int kk = 0; kk < BKC; ++kk) {
           const int k = k0 + kk;
-          vb[kk] = (j < N && k < K) ? B[(long long)k * ldb + j] : make_float2(0.f, 0.f);
+          vb[kk] = (j < N && k < kend) ? B[(long long)k * ldb + j] : make_float2(0.f, 0.f);
         }
       } else {
         const float2* src = B + (long long)j * ldb + k0;
 #pragma unroll
         for (int kk = 0; kk < BKC; ++kk) {
-          float2 v = (j < N && k0 + kk < K) ? src[kk] : make_float2(0.f, 0.f);
+          float2 v = (j < N && k0 + kk < kend) ? src[kk] : make_float2(0.f, 0.f);
           v.y = -v.y;
           vb[kk] = v;
         }
@@ -343,16 +345,70 @@ int* tc_error_ptr() {
   return ptrs[dev];
 }
 
+// C[z] = alpha sum_s P[z * S + s] + beta C[z]: the K-slices of a split GEMM added in slice order.
+__global__ void __launch_bounds__(256) cgemm_split_reduce_kernel(int M, int N, int S, const float2* __restrict__ P,
+                                                                 float2 alpha, float2 beta, float2* __restrict__ C,
+                                                                 long long sC, int ldc) {
+  const int z = blockIdx.y;
+  const long long mn = (long long)M * N;
+  const bool use_beta = (beta.x != 0.f || beta.y != 0.f);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < mn;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    float2 a = make_float2(0.f, 0.f);
+    for (int s = 0; s < S; ++s) {
+      const float2 p = P[((long long)z * S + s) * mn + idx];
+      a.x += p.x;
+      a.y += p.y;
+    }
+    float2 v = make_float2(alpha.x * a.x - alpha.y * a.y, alpha.x * a.y + alpha.y * a.x);
+    float2* c = C + z * sC + (long long)i * ldc + j;
+    if (use_beta) {
+      const float2 o = *c;
+      v.x += beta.x * o.x - beta.y * o.y;
+      v.y += beta.x * o.y + beta.y * o.x;
+    }
+    *c = v;
+  }
+}
+
 template <int OPA, int OPB>
 static cudaError_t launch_tc(cudaStream_t st, int M, int N, int K, float2 alpha, const float2* A, long long sA, int lda,
                              const float2* B, long long sB, int ldb, float2 beta, float2* C, long long sC, int ldc,
                              int batch, int* err) {
   cudaError_t e0 = ensure_kernel_smem((const void*)cgemm_tc_kernel<OPA, OPB>, tc::SMEM_BYTES, false);
   if (e0 != cudaSuccess) return e0;
-  dim3 grid((N + tc::BN - 1) / tc::BN, (M + tc::BM - 1) / tc::BM, batch);
-  cgemm_tc_kernel<OPA, OPB><<<grid, 256, tc::SMEM_BYTES, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC,
-                                                                ldc, err);
-  return cudaGetLastError();
+  const int tiles = ((N + tc::BN - 1) / tc::BN) * ((M + tc::BM - 1) / tc::BM) * batch;
+  // split K when the tiles leave most of the 152 SMs idle and K is long: about two CTAs per SM,
+  // slices of at least 256 complex K
+  int S = 1;
+  if (tiles < 152 && K >= 512) S = std::min(16, std::min((2 * 152 + tiles - 1) / tiles, K / 256));
+  int kc = (K + S - 1) / S;
+  kc = (kc + tc::BKC - 1) / tc::BKC * tc::BKC;
+  S = std::max(1, (K + kc - 1) / kc);
+  if (S == 1) {
+    dim3 grid((N + tc::BN - 1) / tc::BN, (M + tc::BM - 1) / tc::BM, batch);
+    cgemm_tc_kernel<OPA, OPB><<<grid, 256, tc::SMEM_BYTES, st>>>(M, N, K, alpha, A, sA, lda, B, sB, ldb, beta, C, sC,
+                                                                  ldc, 1, K, err);
+    return cudaGetLastError();
+  }
+  float2* P = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&P, sizeof(float2) * (size_t)M * N * S * batch, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((N + tc::BN - 1) / tc::BN, (M + tc::BM - 1) / tc::BM, batch * S);
+  cgemm_tc_kernel<OPA, OPB><<<grid, 256, tc::SMEM_BYTES, st>>>(M, N, K, make_float2(1.f, 0.f), A, sA, lda, B, sB,
+                                                                ldb, make_float2(0.f, 0.f), P, (long long)M * N, N, S,
+                                                                kc, err);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    const long long mn = (long long)M * N;
+    const int blocks = (int)std::min<long long>((mn + 255) / 256, 2048);
+    cgemm_split_reduce_kernel<<<dim3(blocks, batch), 256, 0, st>>>(M, N, S, P, alpha, beta, reinterpret_cast<float2*>(C),
+                                                                   sC, ldc);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(P, st);
+  return e;
 }
 
 cudaError_t cgemm_tc(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<float> alpha, const cx<float>* A,

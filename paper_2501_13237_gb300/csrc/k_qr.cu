@@ -45,7 +45,7 @@ struct QrMsg {
 template <typename R>
 __global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(cx<R>* Ab, long long sA, int lda, int m, int pb, int bw,
                                                                cx<R>* Vb, long long sV, int ldv, cx<R>* Tb,
-                                                               long long sT, int maxloc) {
+                                                               long long sT, int maxloc, int zr) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -253,8 +253,12 @@ __global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(cx<R>* Ab, long lo
     V[gi * ldv + pb + c] = pi >= c ? val : mk<R>(0, 0);
     A[gi * lda + pb + c] = pi < c ? val : (pi == c ? alphas[c] : mk<R>(0, 0));
   }
-  if (rank == 0)
+  if (rank == 0) {
     for (int e = tid; e < QB * QB; e += QR_THREADS) T[e] = Ts[e / QB][e % QB];
+    // rows of the outer block above this panel: zero in its reflector columns
+    for (int e = tid; e < zr * QB; e += QR_THREADS)
+      if (e % QB < bw) V[(long long)(pb - zr + e / QB) * ldv + pb + e % QB] = mk<R>(0, 0);
+  }
 }
 
 // Shared-memory state of one register-resident panel factorisation.  Norm
@@ -362,7 +366,7 @@ __device__ __forceinline__ void panel_norm_round(R sacc, cx<R> x0_mine, bool hol
 template <typename R, int RPW>
 __global__ void __launch_bounds__(QR_THREADS) qr_panel_reg_kernel(cx<R>* Ab, long long sA, int lda, int m, int pb,
                                                                    int bw, cx<R>* Vb, long long sV, int ldv,
-                                                                   cx<R>* Tb, long long sT) {
+                                                                   cx<R>* Tb, long long sT, int zr) {
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -572,8 +576,58 @@ __global__ void __launch_bounds__(QR_THREADS) qr_panel_reg_kernel(cx<R>* Ab, lon
       A[gi * lda + pb + lane] = pi < lane ? a[k] : (pi == lane ? sh.alphas[lane] : mk<R>(0, 0));
     }
   }
-  if (rank == 0)
+  if (rank == 0) {
     for (int e = tid; e < QB * QB; e += QR_THREADS) T[e] = sh.Ts[e / QB][e % QB];
+    // rows of the outer block above this panel: zero in its reflector columns
+    for (int e = tid; e < zr * QB; e += QR_THREADS)
+      if (e % QB < bw) V[(long long)(pb - zr + e / QB) * ldv + pb + e % QB] = mk<R>(0, 0);
+  }
+}
+
+constexpr int QNB = 128;   // outer block: 4 panels applied to the trailing matrix together
+
+// Compact-WY factor of an outer block of np_in <= 4 panels from the panels'
+// factors T_a (32 x 32, upper) and the Gram G = V^H V of the block's
+// reflectors (nbw x nbw): the product of the panels' block reflectors is
+// I - V T V^H with T upper triangular, T_aa = T_a and, block column by block
+// column, T[0:a, a] = -T[0:a, 0:a] G[0:a, a] T_a.  One CTA per matrix;
+// writes T (QNB x QNB, zero outside nbw x nbw).
+template <typename R>
+__global__ void __launch_bounds__(256) wy_merge_t_kernel(const cx<R>* Tpb, long long sTp, const cx<R>* Gb, long long sG,
+                                                         int nbw, cx<R>* Tob, long long sTo) {
+  extern __shared__ unsigned char smem_raw[];
+  cx<R>* X = reinterpret_cast<cx<R>*>(smem_raw);   // [(QNB - QB)][QB + 1]
+  const int z = blockIdx.x, tid = threadIdx.x;
+  const cx<R>* Tp = Tpb + z * sTp;
+  const cx<R>* G = Gb + z * sG;
+  cx<R>* T = Tob + z * sTo;
+  const int np_in = (nbw + QB - 1) / QB;
+  for (int e = tid; e < QNB * QNB; e += 256) {
+    const int r = e / QNB, c = e % QNB;
+    const int a = r / QB, b = c / QB;
+    T[e] = (a == b && a < np_in) ? Tp[(long long)a * QB * QB + (r % QB) * QB + (c % QB)] : mk<R>(0, 0);
+  }
+  __syncthreads();
+  for (int b = 1; b < np_in; ++b) {
+    const int rows = b * QB, c0 = b * QB;
+    // X = T[0:rows, 0:rows] G[0:rows, c0:c0+32]   (T upper triangular)
+    for (int e = tid; e < rows * QB; e += 256) {
+      const int r = e / QB, c = e % QB;
+      cx<R> acc = mk<R>(0, 0);
+      if (c0 + c < nbw)
+        for (int l = r; l < rows; ++l) fma_(acc, T[(long long)r * QNB + l], G[(long long)l * nbw + c0 + c]);
+      X[r * (QB + 1) + c] = acc;
+    }
+    __syncthreads();
+    // T[0:rows, c0:c0+32] = -X T_b   (T_b upper triangular)
+    for (int e = tid; e < rows * QB; e += 256) {
+      const int r = e / QB, c = e % QB;
+      cx<R> acc = mk<R>(0, 0);
+      for (int l = 0; l <= c; ++l) fma_(acc, X[r * (QB + 1) + l], T[(long long)(c0 + l) * QNB + c0 + c]);
+      T[(long long)r * QNB + c0 + c] = mk<R>(-acc.re, -acc.im);
+    }
+    __syncthreads();
+  }
 }
 
 template <typename R>
@@ -611,67 +665,118 @@ QrWork qr_workspace(int m, int n) {
   QrWork w;
   const int k = std::min(m, n);
   const int np = (k + QB - 1) / QB;
-  // V (m x n) + T (np x 32 x 32) + WY application workspace (n columns)
-  w.cx_elems = (long long)m * n + (long long)np * QB * QB + wy_workspace(n) + 64;
+  const int nblk = (k + QNB - 1) / QNB;
+  // V (m x n) + panel T (np x 32 x 32) + WY application workspace (n columns)
+  // + block T (nblk x 128 x 128) + Gram (128 x 128) + W1, W2 (128 x n each)
+  w.cx_elems = (long long)m * n + (long long)np * QB * QB + wy_workspace(n) + (long long)nblk * QNB * QNB +
+               (long long)QNB * QNB + 2LL * QNB * n + 64;
   return w;
 }
 
+// Factor the panel A[pb:m, pb:pb+bw] of every matrix (V, its T at Tp); zr rows
+// above pb belong to the same outer block and get zeros in V's panel columns.
+template <typename R>
+static cudaError_t panel_factor(cudaStream_t st, cx<R>* A, long long sA, int m, int n, int pb, int bw, cx<R>* V,
+                                long long sV, cx<R>* Tp, long long sT, int zr, int batch) {
+  const int mp = m - pb;
+  // panel flops: per column j, reflector products and update of the bw-1-j columns to its right
+  // and the v_c^H v_j of the j columns to its left, over mp - j rows (8 real flops per complex MAC)
+  double work = 0;
+  for (int j = 0; j < bw; ++j) work += 8.0 * (double)(mp - j) * (2.0 * (bw - 1 - j) + j + 1);
+  ProfScope ps(st, K_QR_FACTOR, 1, work * batch);
+  // register-resident panel when every CTA's rows fit 16 warps x 16 registers
+  int csr = mp >= 512 ? 8 : (mp >= 128 ? 4 : (mp >= 32 ? 2 : 1));
+  if ((mp + csr - 1) / csr > 16 * QR_WARPS) csr = 16;
+  const int nl = (mp + csr - 1) / csr;
+  if (nl <= 1 * QR_WARPS)
+    return launch_cluster_qr(qr_panel_reg_kernel<R, 1>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT, zr);
+  if (nl <= 2 * QR_WARPS)
+    return launch_cluster_qr(qr_panel_reg_kernel<R, 2>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT, zr);
+  if (nl <= 4 * QR_WARPS)
+    return launch_cluster_qr(qr_panel_reg_kernel<R, 4>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT, zr);
+  if (nl <= 8 * QR_WARPS)
+    return launch_cluster_qr(qr_panel_reg_kernel<R, 8>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT, zr);
+  if (nl <= 16 * QR_WARPS)
+    return launch_cluster_qr(qr_panel_reg_kernel<R, 16>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT,
+                             zr);
+  int cs = mp >= 512 ? 8 : (mp >= 128 ? 4 : (mp >= 32 ? 2 : 1));
+  int maxloc = (mp + cs - 1) / cs;
+  size_t smem = sizeof(cx<R>) * (size_t)maxloc * PS;
+  if (smem > 160 * 1024) {
+    cs = 16;
+    maxloc = (mp + cs - 1) / cs;
+    smem = sizeof(cx<R>) * (size_t)maxloc * PS;
+  }
+  return launch_cluster_qr(qr_panel_kernel<R>, cs, batch, smem, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT, maxloc, zr);
+}
+
+// Blocked Householder QR.  Outer blocks of 128 columns: their four 32-column
+// panels are factored and applied to the rest of the block one at a time
+// (wy_apply); the block's reflectors are then merged into one compact-WY
+// factor (Gram V^H V and wy_merge_t) and applied to the trailing columns, and
+// later to Q, with three GEMMs each (tensor cores for complex64).
 template <typename R>
 cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, long long sQ, cx<R>* Rout,
                long long sR, void* cx_ws, int batch) {
   const int k = std::min(m, n);
   if (k <= 0 || batch <= 0) return cudaSuccess;
-  const int np = (k + QB - 1) / QB;
+  const int np = (k + QB - 1) / QB, nblk = (k + QNB - 1) / QNB;
   cx<R>* V = reinterpret_cast<cx<R>*>(cx_ws);
   const long long sV = (long long)m * n;
   cx<R>* T = V + sV * batch;
   const long long sT = (long long)np * QB * QB;
   cx<R>* wyws = T + sT * batch;
+  cx<R>* Tb = wyws + wy_workspace(n) * batch;
+  const long long sTb = (long long)nblk * QNB * QNB;
+  cx<R>* G = Tb + sTb * batch;
+  const long long sG = (long long)QNB * QNB;
+  cx<R>* W1 = G + sG * batch;
+  const long long sW = (long long)QNB * n;
+  cx<R>* W2 = W1 + sW * batch;
+  const cx<R> one = mk<R>(1, 0), zero = mk<R>(0, 0), mone = mk<R>(-1, 0);
+  const size_t merge_smem = sizeof(cx<R>) * (QNB - QB) * (QB + 1);
   cudaError_t e;
-  for (int p = 0; p < np; ++p) {
-    const int pb = p * QB, bw = std::min(QB, k - pb);
-    const int mp = m - pb;
-    int cs = mp >= 512 ? 8 : (mp >= 128 ? 4 : (mp >= 32 ? 2 : 1));
-    int maxloc = (mp + cs - 1) / cs;
-    size_t smem = sizeof(cx<R>) * (size_t)maxloc * PS;
-    if (smem > 160 * 1024) {
-      cs = 16;
-      maxloc = (mp + cs - 1) / cs;
-      smem = sizeof(cx<R>) * (size_t)maxloc * PS;
+  if ((e = ensure_kernel_smem((const void*)wy_merge_t_kernel<R>, merge_smem, false)) != cudaSuccess) return e;
+  for (int b = 0; b < nblk; ++b) {
+    const int b0 = b * QNB, bend = std::min(k, b0 + QNB), nbw = bend - b0, mpb = m - b0;
+    for (int pb = b0; pb < bend; pb += QB) {
+      const int bw = std::min(QB, bend - pb), mp = m - pb, p = pb / QB;
+      if ((e = panel_factor<R>(st, A, sA, m, n, pb, bw, V, sV, T + p * QB * QB, sT, pb - b0, batch)) != cudaSuccess)
+        return e;
+      const int nt_in = bend - pb - bw;
+      if (nt_in > 0) {
+        // rest of the block: A_t <- (I - V T V^H)^H A_t
+        cx<R>* Vp = V + (long long)pb * n + pb;
+        cx<R>* At = A + (long long)pb * n + pb + bw;
+        if ((e = wy_apply<R>(st, false, Vp, sV, n, T + p * QB * QB, sT, QB, true, bw, mp, nt_in, At, sA, n, wyws,
+                             batch)) != cudaSuccess)
+          return e;
+      }
     }
+    // block factor: G = V_b^H V_b, then T_b
+    cx<R>* Vb = V + (long long)b0 * n + b0;
+    if ((e = cgemm<R>(st, OP_C, OP_N, nbw, nbw, mpb, one, Vb, sV, n, Vb, sV, n, zero, G, sG, nbw, batch)) !=
+        cudaSuccess)
+      return e;
     {
-      // panel flops: per column j, reflector products and update of the bw-1-j columns to its right
-      // and the v_c^H v_j of the j columns to its left, over mp - j rows (8 real flops per complex MAC)
-      double work = 0;
-      for (int j = 0; j < bw; ++j) work += 8.0 * (double)(mp - j) * (2.0 * (bw - 1 - j) + j + 1);
-      ProfScope ps(st, K_QR_FACTOR, 1, work * batch);
-      // register-resident panel when every CTA's rows fit 16 warps x 16 registers
-      int csr = mp >= 512 ? 8 : (mp >= 128 ? 4 : (mp >= 32 ? 2 : 1));
-      if ((mp + csr - 1) / csr > 16 * QR_WARPS) csr = 16;
-      const int nl = (mp + csr - 1) / csr;
-      cx<R>* Tp = T + p * QB * QB;
-      if (nl <= 1 * QR_WARPS)
-        e = launch_cluster_qr(qr_panel_reg_kernel<R, 1>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
-      else if (nl <= 2 * QR_WARPS)
-        e = launch_cluster_qr(qr_panel_reg_kernel<R, 2>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
-      else if (nl <= 4 * QR_WARPS)
-        e = launch_cluster_qr(qr_panel_reg_kernel<R, 4>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
-      else if (nl <= 8 * QR_WARPS)
-        e = launch_cluster_qr(qr_panel_reg_kernel<R, 8>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
-      else if (nl <= 16 * QR_WARPS)
-        e = launch_cluster_qr(qr_panel_reg_kernel<R, 16>, csr, batch, 0, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT);
-      else
-        e = launch_cluster_qr(qr_panel_kernel<R>, cs, batch, smem, st, A, sA, n, m, pb, bw, V, sV, n, Tp, sT,
-                              maxloc);
+      ProfScope ps(st, K_WY);
+      wy_merge_t_kernel<R><<<batch, 256, merge_smem, st>>>(T + (b0 / QB) * QB * QB, sT, G, sG, nbw,
+                                                           Tb + (long long)b * QNB * QNB, sTb);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (e != cudaSuccess) return e;
-    const int nt = n - pb - bw;
-    if (nt > 0) {
-      cx<R>* Vp = V + (long long)pb * n + pb;
-      cx<R>* At = A + (long long)pb * n + pb + bw;
-      // A_t <- (I - V T V^H)^H A_t
-      if ((e = wy_apply<R>(st, false, Vp, sV, n, T + p * QB * QB, sT, QB, true, bw, mp, nt, At, sA, n, wyws,
-                           batch)) != cudaSuccess)
+    const int ntr = n - bend;
+    if (ntr > 0) {
+      // trailing columns: C <- (I - V_b T_b V_b^H)^H C
+      cx<R>* Ct = A + (long long)b0 * n + bend;
+      cx<R>* Tbb = Tb + (long long)b * QNB * QNB;
+      if ((e = cgemm<R>(st, OP_C, OP_N, nbw, ntr, mpb, one, Vb, sV, n, Ct, sA, n, zero, W1, sW, ntr, batch)) !=
+          cudaSuccess)
+        return e;
+      if ((e = cgemm<R>(st, OP_C, OP_N, nbw, ntr, nbw, one, Tbb, sTb, QNB, W1, sW, ntr, zero, W2, sW, ntr, batch)) !=
+          cudaSuccess)
+        return e;
+      if ((e = cgemm<R>(st, OP_N, OP_N, mpb, ntr, nbw, mone, Vb, sV, n, W2, sW, ntr, one, Ct, sA, n, batch)) !=
+          cudaSuccess)
         return e;
     }
   }
@@ -681,13 +786,19 @@ cudaError_t qr(cudaStream_t st, cx<R>* A, long long sA, int m, int n, cx<R>* Q, 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = identity<R>(st, Q, sQ, m, k, batch)) != cudaSuccess) return e;
-  for (int p = np - 1; p >= 0; --p) {
-    const int pb = p * QB, bw = std::min(QB, k - pb);
-    const int mp = m - pb, kc = k - pb;
-    cx<R>* Vp = V + (long long)pb * n + pb;
-    cx<R>* Qp = Q + (long long)pb * k + pb;
-    // Q_p <- (I - V T V^H) Q_p
-    if ((e = wy_apply<R>(st, false, Vp, sV, n, T + p * QB * QB, sT, QB, false, bw, mp, kc, Qp, sQ, k, wyws, batch)) !=
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int b0 = b * QNB, nbw = std::min(k, b0 + QNB) - b0, mpb = m - b0, kc = k - b0;
+    cx<R>* Vb = V + (long long)b0 * n + b0;
+    cx<R>* Qb = Q + (long long)b0 * k + b0;
+    cx<R>* Tbb = Tb + (long long)b * QNB * QNB;
+    // Q_b <- (I - V_b T_b V_b^H) Q_b
+    if ((e = cgemm<R>(st, OP_C, OP_N, nbw, kc, mpb, one, Vb, sV, n, Qb, sQ, k, zero, W1, sW, kc, batch)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cgemm<R>(st, OP_N, OP_N, nbw, kc, nbw, one, Tbb, sTb, QNB, W1, sW, kc, zero, W2, sW, kc, batch)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cgemm<R>(st, OP_N, OP_N, mpb, kc, nbw, mone, Vb, sV, n, W2, sW, kc, one, Qb, sQ, k, batch)) !=
         cudaSuccess)
       return e;
   }

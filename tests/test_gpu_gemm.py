@@ -25,7 +25,8 @@ def op(a, o):
 
 @pytest.mark.parametrize("tc", [1, 0])
 @pytest.mark.parametrize("opa,opb", [(0, 0), (0, 1), (1, 0), (1, 1)])
-@pytest.mark.parametrize("M,N,K", [(200, 150, 77), (128, 128, 16), (256, 384, 512), (65, 300, 33), (512, 64, 1024)])
+@pytest.mark.parametrize("M,N,K", [(200, 150, 77), (128, 128, 16), (256, 384, 512), (65, 300, 33), (512, 64, 1024),
+                                   (128, 96, 2055)])   # the last three split K over CTAs (few tiles, long K)
 def test_cgemm_vs_float64(env, tc, opa, opb, M, N, K):
     torch, nne, ctx = env
     nne.set_option(nne.OPT_TENSOR_CORES, tc)
