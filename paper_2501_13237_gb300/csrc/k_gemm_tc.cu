@@ -23,11 +23,19 @@ namespace nne {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BKC = 16;       // tile rows, complex columns, complex K per chunk
-constexpr int STAGES = 3;
-constexpr int PLANE = BM * BKC * 4;               // bytes of one 128 x 16 tf32 plane (8 KB)
+constexpr int BM = 128, BN = 128, BKC = 8;        // tile rows, complex columns, complex K per chunk (one MMA K)
+constexpr int STAGES = 3;                         // split-operand stages read by the MMAs
+constexpr int PLANE = BM * BKC * 4;               // bytes of one 128 x 8 tf32 plane (4 KB)
 constexpr int STAGE_BYTES = 8 * PLANE;            // A: ar_hi ai_hi ar_lo ai_lo, B: br_hi bi_hi br_lo bi_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+// raw complex64 operand stages filled by cp.async: a 128 x 8 block either row-major with rows
+// padded to 10 elements (80 B: 16-byte reads of 8 consecutive rows hit distinct banks) or
+// k-major 8 x 128
+constexpr int RAW_STAGES = 4;
+constexpr int RAW_LD = BKC + 2;
+constexpr int RAW_OP_BYTES = BM * RAW_LD * 8;     // 10 KB (>= the 8 KB k-major form)
+constexpr int RAW_STAGE_BYTES = 2 * RAW_OP_BYTES;
+constexpr int RAW_OFFSET = STAGES * STAGE_BYTES;
+constexpr int SMEM_BYTES = RAW_OFFSET + RAW_STAGES * RAW_STAGE_BYTES + 1024;
 constexpr long long SPIN_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -35,16 +43,16 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 }
 
 // Canonical K-major layout, no swizzle: core matrices of 8 rows x 16 bytes;
-// row groups SBO = 512 B apart, K groups LBO = 128 B apart.
+// row groups SBO = 256 B apart (8 tf32 of K per row group), K groups LBO = 128 B apart.
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)((row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+  return (uint32_t)((row >> 3) * 256 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
   d |= (uint64_t)((128 >> 4) & 0x3FFF) << 16;   // leading byte offset (K direction)
-  d |= (uint64_t)((512 >> 4) & 0x3FFF) << 32;   // stride byte offset (8-row groups)
+  d |= (uint64_t)((256 >> 4) & 0x3FFF) << 32;   // stride byte offset (8-row groups)
   d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
   return d;                                     // base offset 0, no swizzle
 }
@@ -85,6 +93,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 8-byte asynchronous copy global -> shared; bytes beyond src_bytes (0 or 8) are zero-filled.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Barrier 2 over the 128 producer threads that also returns the OR of `flag` over them, so every
+// producer takes the same branch afterwards.
+__device__ __forceinline__ bool producers_sync_or(bool flag) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 2, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)flag)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void cp_async_wait_stages() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(RAW_STAGES - 2) : "memory");
+}
 
 __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t id, uint32_t acc) {
   asm volatile(
@@ -168,53 +196,94 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
   const uint32_t tbase = tmem_base;
 
   if (warp < 4) {
-    // ---------------- producers: thread t owns tile row t of A and tile column t of B.
-    // The next chunk's operands are loaded into registers while the current one
-    // is split and stored, so global-load latency overlaps the MMAs.
+    // ---------------- producers (128 threads).  Raw complex64 operands of chunk c + RAW_STAGES - 1
+    // are copied asynchronously while chunk c is split into hi/lo tf32 planes (thread t: tile
+    // row t of A and tile column t of B); the split stages feed the MMAs through mbarriers.
     const int t = threadIdx.x;
-    float2 va[BKC], vb[BKC];
-    auto load_chunk = [&](int c) {
-      const int k0 = kbeg + c * BKC;
-      const int i = row0 + t, j = col0 + t;
-      if (OPA == OP_N) {
-        const float2* src = A + (long long)i * lda + k0;
+    unsigned char* raw0 = smem + RAW_OFFSET;
+    // A is "row-major" in the raw stage when its rows hold K (op N), B when its columns do (op C)
+    constexpr bool A_RM = OPA == OP_N, B_RM = OPB == OP_C;
+    auto issue = [&](int c) {
+      if (c < nchunks) {
+        const int k0 = kbeg + c * BKC;
+        unsigned char* ra = raw0 + (c % RAW_STAGES) * RAW_STAGE_BYTES;
+        unsigned char* rb = ra + RAW_OP_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < BKC; ++kk) va[kk] = (i < M && k0 + kk < kend) ? src[kk] : make_float2(0.f, 0.f);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < BKC; ++kk) {
-          const int k = k0 + kk;
-          float2 v = (i < M && k < kend) ? A[(long long)k * lda + i] : make_float2(0.f, 0.f);
-          v.y = -v.y;
-          va[kk] = v;
+        for (int q8 = 0; q8 < BKC; ++q8) {
+          const int q = t + 128 * q8;
+          // A
+          {
+            int i, kk;
+            if (A_RM) { i = q / BKC; kk = q % BKC; } else { kk = q / BM; i = q % BM; }
+            const int gi = row0 + i, gk = k0 + kk;
+            const bool ok = gi < M && gk < kend;
+            const float2* src = ok ? (A_RM ? A + (long long)gi * lda + gk : A + (long long)gk * lda + gi) : A;
+            const int off = A_RM ? (i * RAW_LD + kk) : (kk * BM + i);
+            cp_async8(smem_u32(ra + off * 8), src, ok ? 8u : 0u);
+          }
+          // B
+          {
+            int j, kk;
+            if (B_RM) { j = q / BKC; kk = q % BKC; } else { kk = q / BN; j = q % BN; }
+            const int gj = col0 + j, gk = k0 + kk;
+            const bool ok = gj < N && gk < kend;
+            const float2* src = ok ? (B_RM ? B + (long long)gj * ldb + gk : B + (long long)gk * ldb + gj) : B;
+            const int off = B_RM ? (j * RAW_LD + kk) : (kk * BN + j);
+            cp_async8(smem_u32(rb + off * 8), src, ok ? 8u : 0u);
+          }
         }
       }
-      if (OPB == OP_N) {
-#pragma unroll
-        for (int kk = 0; kk < BKC; ++kk) {
-          const int k = k0 + kk;
-          vb[kk] = (j < N && k < kend) ? B[(long long)k * ldb + j] : make_float2(0.f, 0.f);
-        }
-      } else {
-        const float2* src = B + (long long)j * ldb + k0;
-#pragma unroll
-        for (int kk = 0; kk < BKC; ++kk) {
-          float2 v = (j < N && k0 + kk < kend) ? src[kk] : make_float2(0.f, 0.f);
-          v.y = -v.y;
-          vb[kk] = v;
-        }
-      }
+      cp_async_commit();   // possibly empty: keeps the group count uniform
     };
-    if (nchunks > 0) load_chunk(0);
+    for (int c = 0; c < RAW_STAGES - 1; ++c) issue(c);
     for (int c = 0; c < nchunks; ++c) {
+      cp_async_wait_stages();                           // this thread's copies of chunk c landed
+      // everyone's copies landed and everyone is done reading chunk c-1; all agree on aborting
+      if (producers_sync_or(*(volatile int*)&abort_flag != 0)) break;
+      issue(c + RAW_STAGES - 1);                        // into the stage chunk c-1 used
       const int s = c % STAGES;
       if (c >= STAGES) {
-        if (!mbar_wait(&empty_bar[s], ((c / STAGES) - 1) & 1)) {
-          atomicExch(&abort_flag, 1);
+        // one thread waits (bounded) for the MMAs to release the stage; the vote spreads the outcome
+        bool ok = true;
+        if (t == 0) ok = mbar_wait(&empty_bar[s], ((c / STAGES) - 1) & 1);
+        if (producers_sync_or(!ok)) {
+          if (t == 0) atomicExch(&abort_flag, 1);
           break;
         }
       }
-      if (*(volatile int*)&abort_flag) break;
+      const unsigned char* ra = raw0 + (c % RAW_STAGES) * RAW_STAGE_BYTES;
+      const unsigned char* rb = ra + RAW_OP_BYTES;
+      float2 va[BKC], vb[BKC];
+      if (A_RM) {
+        const float4* r4 = reinterpret_cast<const float4*>(ra + t * RAW_LD * 8);
+#pragma unroll
+        for (int h = 0; h < BKC / 2; ++h) {
+          const float4 x = r4[h];
+          va[2 * h] = make_float2(x.x, x.y);
+          va[2 * h + 1] = make_float2(x.z, x.w);
+        }
+      } else {
+        const float2* r2 = reinterpret_cast<const float2*>(ra);
+#pragma unroll
+        for (int kk = 0; kk < BKC; ++kk) {
+          float2 v = r2[kk * BM + t];
+          v.y = -v.y;                                   // op C: conjugate
+          va[kk] = v;
+        }
+      }
+      if (B_RM) {
+        const float4* r4 = reinterpret_cast<const float4*>(rb + t * RAW_LD * 8);
+#pragma unroll
+        for (int h = 0; h < BKC / 2; ++h) {
+          const float4 x = r4[h];
+          vb[2 * h] = make_float2(x.x, -x.y);           // op C: conjugate
+          vb[2 * h + 1] = make_float2(x.z, -x.w);
+        }
+      } else {
+        const float2* r2 = reinterpret_cast<const float2*>(rb);
+#pragma unroll
+        for (int kk = 0; kk < BKC; ++kk) vb[kk] = r2[kk * BN + t];
+      }
       unsigned char* st = smem + s * STAGE_BYTES;
 #pragma unroll
       for (int q = 0; q < BKC / 4; ++q) put4(st, 0, 1, core_off(t, 4 * q), &va[4 * q]);
@@ -222,8 +291,8 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
       for (int q = 0; q < BKC / 4; ++q) put4(st + 4 * PLANE, 0, 1, core_off(t, 4 * q), &vb[4 * q]);
       fence_async_smem();
       mbar_arrive(&full_bar[s]);
-      if (c + 1 < nchunks) load_chunk(c + 1);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp == 4) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
@@ -242,7 +311,7 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
         // planes: A 0 ar_hi, 1 ai_hi, 2 ar_lo, 3 ai_lo; B 4 br_hi, 5 bi_hi, 6 br_lo, 7 bi_lo
 #pragma unroll
         for (int ks = 0; ks < BKC / 8; ++ks) {
-          const uint32_t ko = ks * 256;
+          const uint32_t ko = ks * 128 * 8;
           const uint64_t arh = smem_desc(base + 0 * PLANE + ko), aih = smem_desc(base + 1 * PLANE + ko);
           const uint64_t arl = smem_desc(base + 2 * PLANE + ko), ail = smem_desc(base + 3 * PLANE + ko);
           const uint64_t brh = smem_desc(base + 4 * PLANE + ko), bih = smem_desc(base + 5 * PLANE + ko);
