@@ -34,6 +34,21 @@ POLY(m): unweighted least squares polynomial of degree m in
 If no fit is possible the status is NOFIT and the value at lambda* is returned
 when lambda* was emulated (the paper's final fallback), else NaN.
 
+Fidelity extrapolation (A) over a bond-dimension ladder D_1 < ... < D_k
+(Sec. 2.2.3 (A); App. B.1):
+  per (lambda, observable), a least-squares straight line of <O>^{(D_j)}
+    against F^{(D_j)} over the k rungs, evaluated at F = 1 (one rung: the
+    value itself; all F equal: their mean, reading);
+  criterion 1 (App. B.1 eq.): lambda stays in Lambda when
+    |(O_k - O_{k-1}) / (F_k - F_{k-1})| (1 - F_k) < |O_k| / 2, with the
+    readings: F_k = 1 gives a left side of 0 (the top rung is exact); equal
+    top fidelities give 0 when O_k = O_{k-1} and infinity otherwise; one rung
+    keeps every lambda.
+  (B) then runs on the surviving lambdas with F^max = F^{(D_k)}; the dip size
+    d is taken over all levels (it describes F^max(lambda), not the fit set);
+    the NOFIT fallback is the D_k emulation at lambda* (Sec. 2.2.3, last
+    paragraph of (B)).
+
 Pins (tests/test_oracle_fit.py): POLY vs numpy.polyfit; EXP_LOGLIN recovers
 exact a e^{-b lambda} data and equals a closed-form weighted line fit written
 independently; EXP3 recovers noiseless a e^{-b lambda} + c and reaches a loss
@@ -84,7 +99,7 @@ def log_weights(lams, log_fid, lam_star: float, d: float) -> np.ndarray:
     return DELTA_F * np.asarray(log_fid, float) - DELTA_D * np.abs(lam_star - np.asarray(lams, float)) / d
 
 
-def exp_loglin(lams, y, log_fid, lam_star: float, y_zero=None):
+def exp_loglin(lams, y, log_fid, lam_star: float, y_zero=None, d=None):
     lams = np.asarray(lams, float)
     y = np.asarray(y, float)
     log_fid = np.zeros_like(lams) if log_fid is None else np.asarray(log_fid, float)
@@ -95,7 +110,8 @@ def exp_loglin(lams, y, log_fid, lam_star: float, y_zero=None):
     keep = (np.abs(y) >= SMALL) & (np.sign(y) == ref_sign)
     if keep.sum() < 2:
         return exp3(lams, y, lam_star)
-    d = dip_size(lams, log_fid)
+    if d is None:
+        d = dip_size(lams, log_fid)
     lw2 = 2.0 * log_weights(lams, log_fid, lam_star, d)[keep]       # log w^2
     x = lams[keep]
     z = np.log(np.abs(y[keep]))
@@ -194,3 +210,80 @@ def extrapolate(method: int, lams, values, lam_star: float, log_fid=None, degree
         else:
             raise ValueError(method)
     return est, st
+
+
+def fidelity_line(o, fid) -> float:
+    """(A): least-squares line of o against fid (k rungs), evaluated at fid = 1."""
+    o = np.asarray(o, float)
+    fid = np.asarray(fid, float)
+    if o.size == 1:
+        return float(o[0])
+    fm, om = fid.mean(), o.mean()
+    sff = float(np.sum((fid - fm) ** 2))
+    if sff == 0.0:
+        return float(om)
+    slope = float(np.sum((fid - fm) * (o - om))) / sff
+    return float(om + slope * (1.0 - fm))
+
+
+def converged(o, fid) -> bool:
+    """Criterion 1 (App. B.1) on the two largest rungs (last two entries)."""
+    o = np.asarray(o, float)
+    fid = np.asarray(fid, float)
+    if o.size < 2:
+        return True
+    ok, ok1, fk, fk1 = o[-1], o[-2], fid[-1], fid[-2]
+    if fk == 1.0:
+        lhs = 0.0
+    elif fk == fk1:
+        lhs = 0.0 if ok == ok1 else math.inf
+    else:
+        lhs = abs((ok - ok1) / (fk - fk1)) * (1.0 - fk)
+    return lhs < abs(ok) / 2.0
+
+
+def ladder(values, log_fid):
+    """values (k, n_lambda, n_obs) at D_1..D_k, log_fid (k, n_lambda) ->
+    (obar (n_lambda, n_obs), conv (n_lambda, n_obs) bool)."""
+    values = np.asarray(values, float)
+    fid = np.exp(np.asarray(log_fid, float))
+    k, nl, no = values.shape
+    obar = np.zeros((nl, no))
+    conv = np.zeros((nl, no), bool)
+    for i in range(nl):
+        for o in range(no):
+            obar[i, o] = fidelity_line(values[:, i, o], fid[:, i])
+            conv[i, o] = converged(values[:, i, o], fid[:, i])
+    return obar, conv
+
+
+def nzne(method: int, lams, values, log_fid, lam_star: float, degree: int = 2, y_zero=None):
+    """(A) then (B): values (k, n_lambda, n_obs), log_fid (k, n_lambda).
+    Returns (estimates[n_obs], status[n_obs], obar, conv)."""
+    lams = np.asarray(lams, float)
+    values = np.asarray(values, float)
+    log_fid = np.asarray(log_fid, float)
+    obar, conv = ladder(values, log_fid)
+    lf_max = log_fid[-1]
+    d_all = dip_size(lams, lf_max)
+    n_obs = values.shape[2]
+    est = np.zeros(n_obs)
+    st = np.zeros(n_obs, int)
+    for o in range(n_obs):
+        m = conv[:, o]
+        x, y, lf = lams[m], obar[m, o], lf_max[m]
+        yz = None if y_zero is None else float(np.asarray(y_zero)[o])
+        if x.size == 0:
+            e, s = float("nan"), NOFIT
+        elif method == M_POLY:
+            e, s = poly(x, y, lam_star, degree)
+        elif method == M_EXP_LOGLIN:
+            e, s = exp_loglin(x, y, lf, lam_star, yz, d=d_all)
+        elif method == M_EXP3:
+            e, s = exp3(x, y, lam_star)
+        else:
+            raise ValueError(method)
+        if s == NOFIT:
+            e = _nofit(lams, values[-1, :, o], lam_star)[0]
+        est[o], st[o] = e, s
+    return est, st, obar, conv

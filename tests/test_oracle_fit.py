@@ -149,3 +149,89 @@ def test_relative_error_definition_matches_table():
         for k in ("single", "nzne"):
             rel = abs(row[k] - row["trajectory"]) / abs(row["trajectory"])
             assert abs(rel - row[k + "_rel"]) < 6e-4
+
+
+# ---------------------------------------------------------------- (A) over a bond-dimension ladder
+
+def test_fidelity_line_matches_polyfit():
+    """The straight line in fidelity is numpy.polyfit(F, O, 1) evaluated at F = 1."""
+    rng = np.random.default_rng(3)
+    for k in (2, 3, 5):
+        F = np.sort(rng.uniform(0.2, 0.99, k))
+        O = rng.standard_normal(k)
+        assert abs(fit.fidelity_line(O, F) - np.polyval(np.polyfit(F, O, 1), 1.0)) < 1e-12
+    # exact on a line: O = a + b F -> a + b
+    F = np.array([0.3, 0.6, 0.8])
+    assert abs(fit.fidelity_line(0.25 - 0.5 * F, F) - (0.25 - 0.5)) < 1e-14
+    assert fit.fidelity_line([0.7], [0.4]) == 0.7
+
+
+def test_criterion_one_is_the_two_point_secant_test():
+    """App. B.1: the criterion holds exactly when the secant through the two
+    largest rungs, extrapolated to F = 1, lands within |O_k| / 2 of O_k."""
+    rng = np.random.default_rng(4)
+    hits = 0
+    for _ in range(200):
+        F = np.sort(rng.uniform(0.1, 0.99, 3))
+        O = rng.standard_normal(3)
+        secant = np.polyval(np.polyfit(F[1:], O[1:], 1), 1.0)
+        want = abs(secant - O[2]) < abs(O[2]) / 2
+        assert fit.converged(O, F) == want
+        hits += want
+    assert 20 < hits < 180
+    # worked cases: slope 0.4 over 1 - F = 0.05 -> 0.02 < 0.26; slope 2 over 0.4 -> 0.8 > 0.15
+    assert fit.converged([0.50, 0.52], [0.90, 0.95])
+    assert not fit.converged([0.1, 0.3], [0.5, 0.6])
+
+
+def test_criterion_one_readings():
+    assert fit.converged([0.2, 0.4], [0.5, 1.0])          # exact top rung
+    assert not fit.converged([0.2, 0.0], [0.5, 1.0])      # ... but a zero value never passes "< |O_k|/2"
+    assert fit.converged([0.3, 0.3], [0.7, 0.7])          # flat step at equal fidelity
+    assert not fit.converged([0.3, 0.4], [0.7, 0.7])      # jump at equal fidelity
+    assert fit.converged([0.3], [0.7])                    # one rung keeps every level
+
+
+def _ladder_data(seed=5, k=3, nl=5, no=4):
+    rng = np.random.default_rng(seed)
+    lams = np.arange(1.0, nl + 1)
+    logf = np.log(np.sort(rng.uniform(0.3, 0.999, (k, nl)), axis=0))
+    base = 0.8 * np.exp(-0.3 * lams)[:, None] * np.ones((nl, no))
+    vals = base[None] + 0.02 * rng.standard_normal((k, nl, no)) * (1 - np.exp(logf))[:, :, None]
+    return lams, vals, logf
+
+
+@pytest.mark.parametrize("method", [fit.M_POLY, fit.M_EXP_LOGLIN, fit.M_EXP3])
+def test_nzne_single_rung_equals_extrapolate(method):
+    lams, vals, logf = _ladder_data(k=1)
+    est, st, obar, conv = fit.nzne(method, lams, vals, logf, 1.0, degree=2)
+    ref, rst = fit.extrapolate(method, lams, vals[0], 1.0, log_fid=logf[0], degree=2)
+    assert conv.all() and np.array_equal(obar, vals[0])
+    assert np.array_equal(st, rst)
+    assert np.allclose(est, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_nzne_drops_unconverged_levels():
+    """Levels failing criterion 1 leave Lambda; the log-linear fit on the rest
+    keeps the dip size of all levels (written out here without nzne)."""
+    lams, vals, logf = _ladder_data(k=3)
+    vals[:, 2, 0] = [0.05, 0.4, 0.1]             # level 3, observable 0: far from converged
+    est, st, obar, conv = fit.nzne(fit.M_EXP_LOGLIN, lams, vals, logf, 1.0)
+    assert not conv[2, 0] and conv[:, 1:].all()
+    m = conv[:, 0]
+    d = fit.dip_size(lams, logf[-1])
+    ref, rst = fit.exp_loglin(lams[m], obar[m, 0], logf[-1][m], 1.0, d=d)
+    assert st[0] == rst and abs(est[0] - ref) < 1e-14
+    pest, pst, _, _ = fit.nzne(fit.M_POLY, lams, vals, logf, 1.0, degree=2)
+    pref, _ = fit.poly(lams[m], obar[m, 0], 1.0, 2)
+    assert abs(pest[0] - pref) < 1e-13
+
+
+def test_nzne_nofit_falls_back_to_top_rung_at_target():
+    lams, vals, logf = _ladder_data(k=2, no=1)
+    logf[0], logf[1] = np.log(0.5), np.log(0.7)
+    vals[0, :, 0] = 0.9
+    vals[1, :, 0] = 0.01                          # every level jumps: nothing converged
+    est, st, obar, conv = fit.nzne(fit.M_EXP_LOGLIN, lams, vals, logf, 1.0)
+    assert not conv.any() and st[0] == fit.NOFIT
+    assert est[0] == vals[1, 0, 0]                # D_max emulation at lambda* = 1
