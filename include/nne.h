@@ -170,6 +170,27 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
  * or NULL for the bits given at creation.  Enqueued on the context stream. */
 nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits);
 
+/* The paper's two-step extrapolation over a bond-dimension ladder
+ * D_1 < ... < D_k (Sec. 2.2.3 (A) and (B); App. B.1).
+ *   values   k x n_lambda x n_obs: Re <O> emulated at each D_j and level (host);
+ *   log_fid  k x n_lambda: log of the emulation fidelity at each D_j and level.
+ * (A) per level and observable: least-squares line of <O> against F over the k
+ *     rungs, evaluated at F = 1 (one rung: the value; equal F: their mean),
+ *     written to obar_out (n_lambda x n_obs) when not NULL;
+ *     criterion 1: the level stays when
+ *     |(O_k - O_{k-1}) / (F_k - F_{k-1})| (1 - F_k) < |O_k| / 2
+ *     (F_k = 1 passes; equal top fidelities pass only when O_k = O_{k-1}; one
+ *     rung keeps every level), 0/1 in conv_out (n_lambda x n_obs) when not NULL.
+ * (B) as nne_extrapolate on the levels passing criterion 1, with the top
+ *     rung's fidelity as F^max and the dip size taken over all levels; when no
+ *     fit is possible the status is NNE_ERR_NOFIT and the estimate is the top
+ *     rung's value at lambda* (NaN if lambda* was not emulated).
+ * Limits: k <= 64, n_lambda <= 64.  Synchronises the context stream. */
+nne_status nne_extrapolate_ladder(nne_ctx* ctx, int k, int n_lambda, const double* lambdas, const double* values,
+                                  const double* log_fid, int n_obs, int method, int degree, double lambda_star,
+                                  const double* y_zero, double* out, int32_t* per_obs_status, double* obar_out,
+                                  uint8_t* conv_out);
+
 /* The fit of nne_extrapolate for callers that cannot allocate device memory
  * when they ask for it (no counterpart in the paper): a request loop whose HBM
  * budget is already committed to resident states, where a new cudaMalloc can

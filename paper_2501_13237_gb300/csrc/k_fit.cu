@@ -13,6 +13,15 @@
 //                b on a 4001-point grid of [-B, B], B = 50/span, then golden
 //                section on the best bracket to 1e-12 B.
 // NOFIT: value at lambda* when lambda* was emulated, else NaN.
+//
+// Fidelity extrapolation (A) over a bond-dimension ladder D_1 < ... < D_k
+// (Sec. 2.2.3 (A); App. B.1), ladder_kernel, one thread per (lambda, obs):
+//   obar = least-squares line of <O>^{(D_j)} against F^{(D_j)}, at F = 1
+//   (one rung: the value; equal fidelities: the mean);
+//   criterion 1: |(O_k - O_{k-1}) / (F_k - F_{k-1})| (1 - F_k) < |O_k| / 2
+//   (F_k = 1: left side 0; F_k = F_{k-1}: 0 if O_k = O_{k-1}, else infinite).
+// The fit then sees only the levels passing criterion 1 (mask), keeps the dip
+// size of all levels, and falls back to the D_k emulation at lambda*.
 #include "kernels.cuh"
 
 namespace nne {
@@ -134,7 +143,7 @@ __device__ void exp3_fit(int nl, const double* lam, const double* y, double ls, 
 }
 
 __device__ void loglin_fit(int nl, const double* lam, const double* y, const double* logf, double ls,
-                           const double* yzero, int o, double* est, int* st) {
+                           const double* yzero, int o, double dgiven, double* est, int* st) {
   int jmin = 0;
   for (int j = 1; j < nl; ++j)
     if (lam[j] < lam[jmin]) jmin = j;
@@ -147,10 +156,10 @@ __device__ void loglin_fit(int nl, const double* lam, const double* y, const dou
     nk += keep[j];
   }
   if (nk < 2) { exp3_fit(nl, lam, y, ls, est, st); return; }
-  // dip size over all supplied levels
-  double d = 1e300;
-  bool found = false;
-  for (int j = 0; j < nl; ++j) {
+  // dip size over all supplied levels (given by the caller when the fit sees a subset)
+  double d = dgiven > 0 ? dgiven : 1e300;
+  bool found = dgiven > 0;
+  for (int j = 0; j < nl && dgiven <= 0; ++j) {
     const double F = exp(logf ? logf[j] : 0.0);
     if (lam[j] > 0 && F > DIP_FID && lam[j] < d) { d = lam[j]; found = true; }
   }
@@ -197,19 +206,93 @@ __device__ void loglin_fit(int nl, const double* lam, const double* y, const dou
   *st = NNE_OK;
 }
 
+__device__ double dip_all(int nl, const double* lam, const double* logf) {
+  double d = 1e300;
+  bool found = false;
+  for (int j = 0; j < nl; ++j) {
+    const double F = exp(logf ? logf[j] : 0.0);
+    if (lam[j] > 0 && F > DIP_FID && lam[j] < d) { d = lam[j]; found = true; }
+  }
+  if (found) return d;
+  double lmin = 1e300, lmax = -1e300;
+  for (int j = 0; j < nl; ++j) { lmin = fmin(lmin, lam[j]); lmax = fmax(lmax, lam[j]); }
+  return lmax - lmin > 0 ? lmax - lmin : 1.0;
+}
+
+// mask (nl x n_obs, lambda-major; null: every level): levels the fit may use;
+// fb (nl x n_obs; null: the fitted values): where the NOFIT fallback reads the
+// value at lambda*.
 __global__ void fit_kernel(int nl, const double* lam, const double* vals, const double* logf, int n_obs, int method,
-                           int degree, double ls, const double* yzero, double* out, int* status) {
+                           int degree, double ls, const double* yzero, const uint8_t* mask, const double* fb,
+                           double* out, int* status) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n_obs) return;
-  double y[FIT_MAXL];
-  for (int j = 0; j < nl; ++j) y[j] = vals[(long long)j * n_obs + o];
+  double y[FIT_MAXL], lc[FIT_MAXL], fc[FIT_MAXL];
+  int m = 0;
+  for (int j = 0; j < nl; ++j) {
+    if (mask && !mask[(long long)j * n_obs + o]) continue;
+    y[m] = vals[(long long)j * n_obs + o];
+    lc[m] = lam[j];
+    fc[m] = logf ? logf[j] : 0.0;
+    ++m;
+  }
+  const double dgiven = mask ? dip_all(nl, lam, logf) : -1.0;
   double est = nan("");
   int st = NNE_ERR_NOFIT;
-  if (method == NNE_FIT_POLY) poly_fit(nl, lam, y, ls, degree, &est, &st);
-  else if (method == NNE_FIT_EXP_LOGLIN) loglin_fit(nl, lam, y, logf, ls, yzero, o, &est, &st);
-  else exp3_fit(nl, lam, y, ls, &est, &st);
+  if (m == 0) {
+    st = NNE_ERR_NOFIT;
+  } else if (method == NNE_FIT_POLY) {
+    poly_fit(m, lc, y, ls, degree, &est, &st);
+  } else if (method == NNE_FIT_EXP_LOGLIN) {
+    loglin_fit(m, lc, y, logf ? fc : nullptr, ls, yzero, o, dgiven, &est, &st);
+  } else {
+    exp3_fit(m, lc, y, ls, &est, &st);
+  }
+  if (st == NNE_ERR_NOFIT && (fb || mask)) {
+    const double* src = fb ? fb : vals;
+    est = nan("");
+    for (int j = 0; j < nl; ++j)
+      if (lam[j] == ls) { est = src[(long long)j * n_obs + o]; break; }
+  }
   out[o] = est;
   status[o] = st;
+}
+
+// (A) over k rungs: vals (k x nl x n_obs), logf (k x nl) -> obar (nl x n_obs), conv (nl x n_obs).
+__global__ void ladder_kernel(int k, int nl, int n_obs, const double* vals, const double* logf, double* obar,
+                              uint8_t* conv) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nl * n_obs) return;
+  const int i = (int)(idx / n_obs), o = (int)(idx % n_obs);
+  auto O = [&](int j) { return vals[((long long)j * nl + i) * n_obs + o]; };
+  auto F = [&](int j) { return exp(logf[(long long)j * nl + i]); };
+  double ob;
+  if (k == 1) {
+    ob = O(0);
+  } else {
+    double fm = 0, om = 0;
+    for (int j = 0; j < k; ++j) { fm += F(j); om += O(j); }
+    fm /= k;
+    om /= k;
+    double sff = 0, sfo = 0;
+    for (int j = 0; j < k; ++j) {
+      const double df = F(j) - fm;
+      sff += df * df;
+      sfo += df * (O(j) - om);
+    }
+    ob = sff == 0.0 ? om : om + (sfo / sff) * (1.0 - fm);
+  }
+  bool c = true;
+  if (k >= 2) {
+    const double ok = O(k - 1), ok1 = O(k - 2), fk = F(k - 1), fk1 = F(k - 2);
+    double lhs;
+    if (fk == 1.0) lhs = 0.0;
+    else if (fk == fk1) lhs = ok == ok1 ? 0.0 : INFINITY;
+    else lhs = fabs((ok - ok1) / (fk - fk1)) * (1.0 - fk);
+    c = lhs < fabs(ok) / 2.0;
+  }
+  obar[idx] = ob;
+  conv[idx] = c ? 1 : 0;
 }
 
 cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, const double* d_vals,
@@ -218,7 +301,24 @@ cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, 
   if (n_obs <= 0) return cudaSuccess;
   ProfScope ps(st, K_FIT);
   fit_kernel<<<(n_obs + 63) / 64, 64, 0, st>>>(n_lambda, d_lam, d_vals, d_logfid, n_obs, method, degree, lambda_star,
-                                              d_yzero, d_out, d_status);
+                                              d_yzero, nullptr, nullptr, d_out, d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t extrapolate_ladder(cudaStream_t st, int k, int n_lambda, const double* d_lam, const double* d_vals,
+                               const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
+                               const double* d_yzero, double* d_obar, uint8_t* d_conv, double* d_out, int* d_status) {
+  if (n_obs <= 0) return cudaSuccess;
+  ProfScope ps(st, K_FIT, 2);
+  const long long cells = (long long)n_lambda * n_obs;
+  ladder_kernel<<<(unsigned)((cells + 127) / 128), 128, 0, st>>>(k, n_lambda, n_obs, d_vals, d_logfid, d_obar, d_conv);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // (B) on the fidelity-extrapolated values, F^max = the top rung, fallback to the top rung's values
+  const double* top_logf = d_logfid + (long long)(k - 1) * n_lambda;
+  const double* top_vals = d_vals + (long long)(k - 1) * cells;
+  fit_kernel<<<(n_obs + 63) / 64, 64, 0, st>>>(n_lambda, d_lam, d_obar, top_logf, n_obs, method, degree, lambda_star,
+                                              d_yzero, d_conv, top_vals, d_out, d_status);
   return cudaGetLastError();
 }
 

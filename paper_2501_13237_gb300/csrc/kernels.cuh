@@ -117,6 +117,11 @@ cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, 
                             const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
                             const double* d_yzero, double* d_out, int* d_status);
 
+// Fidelity extrapolation over a bond-dimension ladder, then the fit (see nne_extrapolate_ladder).
+cudaError_t extrapolate_ladder(cudaStream_t st, int k, int n_lambda, const double* d_lam, const double* d_vals,
+                               const double* d_logfid, int n_obs, int method, int degree, double lambda_star,
+                               const double* d_yzero, double* d_obar, uint8_t* d_conv, double* d_out, int* d_status);
+
 // ---- nne_api.cu
 // Bond capacities min(chi, 4^k, 4^(n-k)), k = 0..n.
 std::vector<int> bond_caps(int n, int chi);

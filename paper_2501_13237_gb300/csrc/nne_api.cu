@@ -838,6 +838,52 @@ nne_status nne_extrapolate(nne_ctx* ctx, int n_lambda, const double* lambdas, co
   return rc;
 }
 
+nne_status nne_extrapolate_ladder(nne_ctx* ctx, int k, int n_lambda, const double* lambdas, const double* values,
+                                  const double* log_fid, int n_obs, int method, int degree, double lambda_star,
+                                  const double* y_zero, double* out, int32_t* per_obs_status, double* obar_out,
+                                  uint8_t* conv_out) {
+  if (!ctx || k < 1 || k > 64 || n_lambda < 1 || n_lambda > 64 || !lambdas || !values || !log_fid || n_obs < 0 ||
+      !out || !per_obs_status || method < 0 || method > 2 || (method == NNE_FIT_POLY && (degree < 1 || degree > 15)))
+    return set_error(NNE_ERR_ARG, "nne_extrapolate_ladder: bad arguments");
+  if (n_obs == 0) return NNE_OK;
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const size_t cells = (size_t)n_lambda * n_obs;
+  double *dl = nullptr, *dv = nullptr, *df = nullptr, *dy = nullptr, *dob = nullptr, *dout = nullptr;
+  uint8_t* dc = nullptr;
+  int* dst = nullptr;
+  NNE_CUDA_TRY(cudaMallocAsync(&dl, sizeof(double) * n_lambda, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dv, sizeof(double) * k * cells, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&df, sizeof(double) * k * (size_t)n_lambda, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dy, sizeof(double) * (size_t)n_obs, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dob, sizeof(double) * cells, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dc, cells, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dout, sizeof(double) * (size_t)n_obs, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dst, sizeof(int) * (size_t)n_obs, s));
+  cudaError_t e = cudaMemcpyAsync(dl, lambdas, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dv, values, sizeof(double) * k * cells, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(df, log_fid, sizeof(double) * k * (size_t)n_lambda, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && y_zero) e = cudaMemcpyAsync(dy, y_zero, sizeof(double) * n_obs, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = extrapolate_ladder(s, k, n_lambda, dl, dv, df, n_obs, method, degree, lambda_star, y_zero ? dy : nullptr, dob,
+                           dc, dout, dst);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(double) * n_obs, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(per_obs_status, dst, sizeof(int) * n_obs, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && obar_out) e = cudaMemcpyAsync(obar_out, dob, sizeof(double) * cells, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && conv_out) e = cudaMemcpyAsync(conv_out, dc, cells, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  nne_status rc = e == cudaSuccess ? NNE_OK : set_cuda_error(e, "nne_extrapolate_ladder", __FILE__, __LINE__);
+  cudaFreeAsync(dl, s);
+  cudaFreeAsync(dv, s);
+  cudaFreeAsync(df, s);
+  cudaFreeAsync(dy, s);
+  cudaFreeAsync(dob, s);
+  cudaFreeAsync(dc, s);
+  cudaFreeAsync(dout, s);
+  cudaFreeAsync(dst, s);
+  return rc;
+}
+
 nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits) {
   if (!st) return set_error(NNE_ERR_ARG, "null state");
   DeviceGuard dg(st->ctx->device);

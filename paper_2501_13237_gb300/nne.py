@@ -31,6 +31,7 @@ SYMBOLS = (
     "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
     "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
+    "nne_extrapolate_ladder",
 )
 SERVER_DRYRUN = 1
 
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
         "nne_poll": (i32, [vp, C.c_uint64, i32, P(ResultStruct)]),
         "nne_server_stats": (None, [vp, P(i32), P(i32), P(i32), P(sz)]),
         "nne_server_destroy": (None, [vp]),
+        "nne_extrapolate_ladder": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -189,6 +191,25 @@ class Context:
                                       float(lambda_star), _hptr(yz), _hptr(out), _hptr(st)))
         return out, st
 
+
+    def extrapolate_ladder(self, lambdas, values, log_fid, method=FIT_EXP_LOGLIN, degree=2, lambda_star=1.0,
+                           y_zero=None):
+        """(A) + (B) over a bond-dimension ladder: values (k, n_lambda, n_obs), log_fid (k, n_lambda).
+        Returns (estimates[n_obs], status[n_obs], obar (n_lambda, n_obs), converged (n_lambda, n_obs))."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        lf = np.ascontiguousarray(log_fid, dtype=np.float64)
+        k, nl, no = v.shape
+        assert lf.shape == (k, nl) and lam.shape == (nl,)
+        yz = None if y_zero is None else np.ascontiguousarray(y_zero, dtype=np.float64)
+        out = np.zeros(no)
+        st = np.zeros(no, dtype=np.int32)
+        ob = np.zeros((nl, no))
+        cv = np.zeros((nl, no), dtype=np.uint8)
+        _check(load().nne_extrapolate_ladder(self.h, k, nl, _hptr(lam), _hptr(v), _hptr(lf), no, method, degree,
+                                             float(lambda_star), _hptr(yz), _hptr(out), _hptr(st), _hptr(ob),
+                                             _hptr(cv)))
+        return out, st, ob, cv.astype(bool)
 
     def extrapolate_noalloc(self, lambdas, values, log_fid=None, method=FIT_EXP_LOGLIN, degree=2,
                             lambda_star=1.0, y_zero=None):

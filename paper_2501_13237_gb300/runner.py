@@ -63,3 +63,18 @@ def job_for(w, chi=None, dtype: int = nne.C64, trunc: int = nne.TRUNC_EXACT, ske
                    pauli_codes(w.observables, w.n) if paulis is None else paulis,
                    dtype=dtype, trunc=trunc, sketch=sketch, power_iters=power_iters, bits=w.bits(),
                    fit_method=fit, fit_degree=degree, lambda_star=w.lambda_star)
+
+
+def emulate_ladder(ctx: nne.Context, circuit, rates: np.ndarray, chis, paulis: np.ndarray, dtype: int = nne.C64,
+                   trunc: int = nne.TRUNC_EXACT, bits=None):
+    """The same circuit at every noise level for each bond dimension of a ladder
+    D_1 < ... < D_k (one state per rung).  Returns values (k, n_inst, n_obs)
+    (real parts) and log F (k, n_inst) for nne_extrapolate_ladder."""
+    layers = build_layer_superops(ctx, circuit, rates)
+    vals, lfs = [], []
+    for chi in chis:
+        st, v, lf = emulate(ctx, circuit, rates, int(chi), paulis, dtype, trunc, bits, layers)
+        st.close()
+        vals.append(v.real)
+        lfs.append(lf)
+    return np.stack(vals), np.stack(lfs)

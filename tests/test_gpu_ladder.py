@@ -1,0 +1,81 @@
+"""Fidelity extrapolation over a bond-dimension ladder and criterion 1
+(Sec. 2.2.3 (A), App. B.1) through nne_extrapolate_ladder, against the
+oracle: crafted ladders that hit every branch, and a chi ladder emulated on
+the GPU next to the oracle MPS at each rung."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from gpu_util import require_gpu
+from oracle import fit, mps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    from paper_2501_13237_gb300 import nne
+    return nne.Context(0)
+
+
+def _crafted(seed, k=3, nl=6, no=24):
+    rng = np.random.default_rng(seed)
+    lams = np.arange(1.0, nl + 1)
+    logf = np.log(np.sort(rng.uniform(0.2, 0.995, (k, nl)), axis=0))
+    base = (0.9 * np.exp(-0.25 * lams))[:, None] * rng.choice([-1.0, 1.0], no)[None, :]
+    vals = base[None] + 0.05 * rng.standard_normal((k, nl, no)) * (1 - np.exp(logf))[:, :, None]
+    if k >= 2:
+        vals[-2, 2, 0], vals[-1, 2, 0] = 0.4, 0.1   # level 3, observable 0: far from converged
+        vals[:-1, :, 1], vals[-1, :, 1] = 0.9, 0.01  # observable 1: large jumps at every level
+        logf[-2, 3] = logf[-1, 3]                    # level 4: equal top fidelities
+    vals[:, :, 2] = vals[-1:, :, 2]                  # observable 2: flat ladder
+    logf[-1, 4] = 0.0                                # level 5: an exact top rung
+    vals[-1, :, 3] = 0.0                             # observable 3: zero values never pass
+    return lams, vals, logf
+
+
+@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("seed,k", [(1, 3), (2, 2), (3, 5), (4, 1)])
+def test_ladder_kernel_vs_oracle(ctx, method, seed, k):
+    lams, vals, logf = _crafted(seed, k=k)
+    est, st, ob, cv = ctx.extrapolate_ladder(lams, vals, logf, method=method, degree=2, lambda_star=1.0)
+    rest, rst, rob, rcv = fit.nzne(method, lams, vals, logf, 1.0, degree=2)
+    assert np.array_equal(cv, rcv)
+    assert np.allclose(ob, rob, rtol=1e-12, atol=1e-14)
+    assert np.array_equal(st, rst)
+    tol = 1e-7 if method == 2 else 1e-10
+    fin = np.isfinite(rest)
+    assert np.array_equal(fin, np.isfinite(est))
+    assert np.allclose(est[fin], rest[fin], rtol=tol, atol=tol)
+    if k >= 2:
+        assert not cv.all()                    # the crafted levels do fail criterion 1
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 2e-4)])
+def test_chi_ladder_emulation_vs_oracle(ctx, dtype, tol):
+    from paper_2501_13237_gb300 import runner
+    n, chis = 8, (16, 32, 64)
+    c = wl.brickwork_circuit(n, 8, 11)
+    noise = wl.NoiseModel(depol2=0.01, amp_damp=0.005, dephase=0.005)
+    lams = np.array([1.0, 2.0, 3.0, 4.0])
+    rates = np.stack([noise.rates(l) for l in lams])
+    paulis = wl.pauli_codes(wl.obs_z(n) + wl.obs_zz(n), n)
+    vals, lfs = runner.emulate_ladder(ctx, c, rates, chis, paulis, dtype)
+    rv = np.zeros_like(vals)
+    rl = np.zeros_like(lfs)
+    for j, chi in enumerate(chis):
+        for i in range(len(lams)):
+            st = mps.run(c, rates[i], chi)
+            rv[j, i] = st.expect_codes(paulis).real
+            rl[j, i] = st.log_fid
+    assert np.abs(vals - rv).max() < tol
+    assert np.abs(lfs - rl).max() < tol * max(1.0, np.abs(rl).max())
+    assert (rl[0] < rl[-1]).all()              # a larger chi keeps more weight
+    est, st, ob, cv = ctx.extrapolate_ladder(lams, vals, lfs, method=1, lambda_star=1.0)
+    rest, rst, rob, rcv = fit.nzne(1, lams, rv, rl, 1.0)
+    assert np.abs(ob - rob).max() < 50 * tol
+    agree = cv == rcv
+    assert agree.mean() > 0.95                 # criterion 1 may flip only at its threshold
+    ok = (st == 0) & (rst == 0) & agree.all(axis=0)
+    assert np.abs(est[ok] - rest[ok]).max() < 100 * tol

@@ -135,3 +135,28 @@ def test_server_many_concurrent_jobs(ctx):
         st.close()
         assert np.array_equal(r["values"], vals.real)
         assert np.array_equal(r["log_fid"], lf)
+
+
+def test_batch_subsample_vs_oracle(ctx):
+    """The multi-circuit batch workload (64 circuits, n 16-64, chi 32-128, five
+    levels of depolarizing + dephasing) runs as concurrent server jobs; an
+    8-circuit subsample, cut to its first six layers so the oracle finishes in
+    seconds, matches the oracle MPS at lambda = 1."""
+    import dataclasses
+    from paper_2501_13237_gb300 import nne, runner
+    ws = []
+    for w in wl.batch64(0)[:8]:
+        c = dataclasses.replace(w.circuit, depth=6, layers=w.circuit.layers[:6], unitaries=w.circuit.unitaries[:6])
+        ws.append(dataclasses.replace(w, circuit=c))
+    srv = nne.Server(0, workers=4)
+    tickets = [srv.submit(runner.job_for(w, dtype=0)) for w in ws]
+    res = [srv.poll(t) for t in tickets]
+    srv.close()
+    assert all(r["status"] == 0 for r in res), [(r["status"], r["error"]) for r in res]
+    for w, r in zip(ws, res):
+        paulis = wl.pauli_codes(w.observables, w.n)
+        ref = mps.run(w.circuit, w.rate_table()[0], w.chi, bits=w.bits())
+        assert np.abs(r["values"][0] - ref.expect_codes(paulis).real).max() < 2e-4
+        # log F sums one complex64-rounded log f per gate (about 1e-5 each): the bound grows with the gates
+        assert abs(r["log_fid"][0] - ref.log_fid) < 2e-5 * w.circuit.n_gates
+        assert r["gate_steps"] == w.circuit.n_gates * len(w.lambdas)
