@@ -157,6 +157,8 @@ def main():
     ap.add_argument("--serving", type=int, default=40,
                     help="requests of the open-loop serving sample added to the line (0: none)")
     ap.add_argument("--serving-rate", type=float, default=20.0, help="offered requests per second")
+    ap.add_argument("--subbatches", type=int, default=None,
+                    help="concurrent sub-batches per state (NNE_OPT_SUBBATCHES; library default when omitted)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -181,6 +183,8 @@ def main():
     paulis = wl.pauli_codes(w.observables, w.n)
     plan = runner.layer_plan(w.circuit)
     ctx = nne.Context(local)
+    if args.subbatches is not None:
+        nne.set_option(nne.OPT_SUBBATCHES, args.subbatches)
     st = nne.State(ctx, w.n, CHI, n_inst, nne.C64, nne.TRUNC_RSVD, w.bits())
     st.set_sketch(wl.gaussian_sketch(4 * CHI, CHI + OVERSAMPLE, 1234).astype(np.complex64), POWER_ITERS)
 

@@ -219,8 +219,16 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
                          const float* beta, void* C, int ldc, long long stride_c, int batch);
 
 /* Library options: NNE_OPT_TENSOR_CORES (default 1) selects the tcgen05 path of
- * complex64 GEMMs (0 = float32 SIMT everywhere, for comparisons). */
+ * complex64 GEMMs (0 = float32 SIMT everywhere, for comparisons).
+ * NNE_OPT_SUBBATCHES (default 4, 1..8) is the number of sub-batches a state
+ * created afterwards splits its instances into for nne_apply_layer: each
+ * sub-batch's gate steps run on a stream of its own (forked from and joined
+ * back to the context stream), so that the latency-bound kernels of one
+ * overlap the GEMMs of another.  States whose largest bond is below 256 use
+ * one stream (their kernels are small and splitting multiplies launches).
+ * Results do not depend on it beyond the rounding of GEMM split choices. */
 #define NNE_OPT_TENSOR_CORES 0
+#define NNE_OPT_SUBBATCHES 1
 void nne_set_option(int option, int value);
 
 /* Wait for the state's enqueued work; returns the first device-side error. */

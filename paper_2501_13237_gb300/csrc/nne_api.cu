@@ -187,6 +187,12 @@ struct nne_state {
   void* eig_re = nullptr;
   void* eig_u8 = nullptr;
   void* qr_ws = nullptr;
+  long long eig_cx_pi = 0, eig_re_pi = 0, eig_u8_pi = 0, qr_pi = 0;   // elements per instance
+  // concurrent sub-batches of the gate steps: each on its own stream
+  int nsub = 1;
+  std::vector<cudaStream_t> sub_st;
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   // sweep
   int* d_dims = nullptr;
   void** d_site = nullptr;
@@ -204,6 +210,19 @@ struct nne_state {
 
 namespace {
 
+// Sub-batches a new state splits its instances into (nne_set_option).
+int g_substreams = 4;
+
+void destroy_streams(nne_state* s) {
+  for (cudaStream_t q : s->sub_st) cudaStreamDestroy(q);
+  for (cudaEvent_t ev : s->ev_join) cudaEventDestroy(ev);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  s->sub_st.clear();
+  s->ev_join.clear();
+  s->ev_fork = nullptr;
+  s->nsub = 1;
+}
+
 template <typename R>
 cx<R>* sp(nne_state* s, int k) { return reinterpret_cast<cx<R>*>(s->site[k]); }
 
@@ -220,73 +239,108 @@ nne_status check(cudaError_t e, const char* what) {
   } while (0)
 #define CTRY(x) TRY(check<R>((x), #x))
 
+// A contiguous range of instances [i0, i0 + nb) whose arithmetic is enqueued
+// on one stream; per-instance buffers are addressed from instance i0.
+struct BatchView {
+  cudaStream_t st;
+  int i0, nb;
+};
+template <typename R>
+cx<R>* spb(nne_state* s, const BatchView& b, int k) {
+  return reinterpret_cast<cx<R>*>(s->site[k]) + (long long)b.i0 * s->sstride[k];
+}
+template <typename R>
+cx<R>* wsb(void* base, long long stride, const BatchView& b) {
+  return reinterpret_cast<cx<R>*>(base) + (long long)b.i0 * stride;
+}
+template <typename R>
+cx<R>* qrws(nne_state* s, const BatchView& b) {
+  return reinterpret_cast<cx<R>*>(s->qr_ws) + (long long)b.i0 * s->qr_pi;
+}
+template <typename R>
+cx<R>* eigcx(nne_state* s, const BatchView& b) {
+  return reinterpret_cast<cx<R>*>(s->eig_cx) + (long long)b.i0 * s->eig_cx_pi;
+}
+template <typename R>
+R* eigre(nne_state* s, const BatchView& b) {
+  return reinterpret_cast<R*>(s->eig_re) + (long long)b.i0 * s->eig_re_pi;
+}
+inline uint8_t* eigu8(nne_state* s, const BatchView& b) {
+  return reinterpret_cast<uint8_t*>(s->eig_u8) + (long long)b.i0 * s->eig_u8_pi;
+}
+
 // Norm bookkeeping after a split: kept = ||C||^2, total = ||X||^2 (or kept).
 template <typename R>
-nne_status finish_split(nne_state* s, cx<R>* C, long long sC, long long countC, const cx<R>* Xt, long long sXt,
+nne_status finish_split(nne_state* s, const BatchView& b, cx<R>* C, long long sC, long long countC, const cx<R>* Xt, long long sXt,
                         long long countX) {
-  cudaStream_t st = s->ctx->stream;
-  double* kept = s->d_parts;
-  double* total = s->d_parts + (long long)s->n_inst * PARTS;
-  CTRY(sumsq_partial<R>(st, C, sC, countC, kept, PARTS, s->n_inst));
-  if (Xt) CTRY(sumsq_partial<R>(st, Xt, sXt, countX, total, PARTS, s->n_inst));
-  CTRY(finish_gate(st, kept, Xt ? total : nullptr, PARTS, s->n_inst, s->d_scale, s->d_lognorm, s->d_logfid, s->d_err));
-  CTRY(scale_batched<R>(st, C, sC, countC, s->d_scale, s->n_inst));
+  cudaStream_t st = b.st;
+  double* kept = s->d_parts + (long long)b.i0 * PARTS;
+  double* total = s->d_parts + (long long)s->n_inst * PARTS + (long long)b.i0 * PARTS;
+  CTRY(sumsq_partial<R>(st, C, sC, countC, kept, PARTS, b.nb));
+  if (Xt) CTRY(sumsq_partial<R>(st, Xt, sXt, countX, total, PARTS, b.nb));
+  CTRY(finish_gate(st, kept, Xt ? total : nullptr, PARTS, b.nb, s->d_scale + b.i0, s->d_lognorm + b.i0, s->d_logfid + b.i0, s->d_err));
+  CTRY(scale_batched<R>(st, C, sC, countC, s->d_scale + b.i0, b.nb));
   return NNE_OK;
 }
 
 // Make site c left-isometric by QR and push R into site c+1.
 template <typename R>
-nne_status qr_right(nne_state* s, int c) {
-  cudaStream_t st = s->ctx->stream;
+nne_status qr_right(nne_state* s, const BatchView& b, int c) {
+  cudaStream_t st = b.st;
   const int dl = s->dims[c], dr = s->dims[c + 1], dn = s->dims[c + 2];
   const int m = 4 * dl, k = std::min(m, dr);
-  cx<R>* M = sp<R>(s, c);
-  cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
-  cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
-  CTRY(qr<R>(st, M, s->sstride[c], m, dr, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));
-  CTRY(fix_qr<R>(st, Q, s->sT, m, k, Rr, s->sR, dr, s->n_inst));
-  CTRY(copy_batched<R>(st, Q, s->sT, M, s->sstride[c], (long long)m * k, s->n_inst));
+  cx<R>* M = spb<R>(s, b, c);
+  cx<R>* Q = wsb<R>(s->T, s->sT, b);
+  cx<R>* Rr = wsb<R>(s->Rm, s->sR, b);
+  CTRY(qr<R>(st, M, s->sstride[c], m, dr, Q, s->sT, Rr, s->sR, qrws<R>(s, b), b.nb));
+  CTRY(fix_qr<R>(st, Q, s->sT, m, k, Rr, s->sR, dr, b.nb));
+  CTRY(copy_batched<R>(st, Q, s->sT, M, s->sstride[c], (long long)m * k, b.nb));
   // next <- R next
-  cx<R>* N = sp<R>(s, c + 1);
-  cx<R>* tmp = reinterpret_cast<cx<R>*>(s->H);
+  cx<R>* N = spb<R>(s, b, c + 1);
+  cx<R>* tmp = wsb<R>(s->H, s->sH, b);
   CTRY(cgemm<R>(st, OP_N, OP_N, k, 4 * dn, dr, mk<R>(1, 0), Rr, s->sR, dr, N, s->sstride[c + 1], 4 * dn,
-                mk<R>(0, 0), tmp, s->sH, 4 * dn, s->n_inst));
-  CTRY(copy_batched<R>(st, tmp, s->sH, N, s->sstride[c + 1], (long long)k * 4 * dn, s->n_inst));
-  s->dims[c + 1] = k;
+                mk<R>(0, 0), tmp, s->sH, 4 * dn, b.nb));
+  CTRY(copy_batched<R>(st, tmp, s->sH, N, s->sstride[c + 1], (long long)k * 4 * dn, b.nb));
   return NNE_OK;
 }
 
 // Make site c right-isometric by LQ (QR of M^H) and push L into site c-1.
 template <typename R>
-nne_status lq_left(nne_state* s, int c) {
-  cudaStream_t st = s->ctx->stream;
+nne_status lq_left(nne_state* s, const BatchView& b, int c) {
+  cudaStream_t st = b.st;
   const int dp = s->dims[c - 1], dl = s->dims[c], dr = s->dims[c + 1];
   const int m = 4 * dr, k = std::min(m, dl);
-  cx<R>* M = sp<R>(s, c);
-  cx<R>* Mh = reinterpret_cast<cx<R>*>(s->U);
-  CTRY(transpose<R>(st, true, M, s->sstride[c], dl, m, m, Mh, s->sU, dl, s->n_inst));   // (4dr x dl)
-  cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
-  cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
-  CTRY(qr<R>(st, Mh, s->sU, m, dl, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));          // Q (m x k), R (k x dl)
-  CTRY(fix_qr<R>(st, Q, s->sT, m, k, Rr, s->sR, dl, s->n_inst));
-  CTRY(transpose<R>(st, true, Q, s->sT, m, k, k, M, s->sstride[c], m, s->n_inst));       // site c = Q^H (k x m)
-  cx<R>* P = sp<R>(s, c - 1);
-  cx<R>* tmp = reinterpret_cast<cx<R>*>(s->H);
+  cx<R>* M = spb<R>(s, b, c);
+  cx<R>* Mh = wsb<R>(s->U, s->sU, b);
+  CTRY(transpose<R>(st, true, M, s->sstride[c], dl, m, m, Mh, s->sU, dl, b.nb));   // (4dr x dl)
+  cx<R>* Q = wsb<R>(s->T, s->sT, b);
+  cx<R>* Rr = wsb<R>(s->Rm, s->sR, b);
+  CTRY(qr<R>(st, Mh, s->sU, m, dl, Q, s->sT, Rr, s->sR, qrws<R>(s, b), b.nb));          // Q (m x k), R (k x dl)
+  CTRY(fix_qr<R>(st, Q, s->sT, m, k, Rr, s->sR, dl, b.nb));
+  CTRY(transpose<R>(st, true, Q, s->sT, m, k, k, M, s->sstride[c], m, b.nb));       // site c = Q^H (k x m)
+  cx<R>* P = spb<R>(s, b, c - 1);
+  cx<R>* tmp = wsb<R>(s->H, s->sH, b);
   CTRY(cgemm<R>(st, OP_N, OP_C, 4 * dp, k, dl, mk<R>(1, 0), P, s->sstride[c - 1], dl, Rr, s->sR, dl, mk<R>(0, 0),
-                tmp, s->sH, k, s->n_inst));
-  CTRY(copy_batched<R>(st, tmp, s->sH, P, s->sstride[c - 1], (long long)4 * dp * k, s->n_inst));
-  s->dims[c] = k;
+                tmp, s->sH, k, b.nb));
+  CTRY(copy_batched<R>(st, tmp, s->sH, P, s->sstride[c - 1], (long long)4 * dp * k, b.nb));
   return NNE_OK;
 }
 
+// Move the orthogonality centre to `target`, one site at a time; each step is
+// enqueued for every batch view (each on its own stream) before the shared
+// bond dimension is updated.
 template <typename R>
-nne_status move_centre(nne_state* s, int target) {
+nne_status move_centre(nne_state* s, const std::vector<BatchView>& views, int target) {
   while (s->centre < target) {
-    TRY(qr_right<R>(s, s->centre));
+    const int c = s->centre;
+    for (const BatchView& b : views) TRY(qr_right<R>(s, b, c));
+    s->dims[c + 1] = std::min(4 * s->dims[c], s->dims[c + 1]);
     s->centre++;
   }
   while (s->centre > target) {
-    TRY(lq_left<R>(s, s->centre));
+    const int c = s->centre;
+    for (const BatchView& b : views) TRY(lq_left<R>(s, b, c));
+    s->dims[c] = std::min(4 * s->dims[c + 1], s->dims[c]);
     s->centre--;
   }
   return NNE_OK;
@@ -300,152 +354,164 @@ nne_status move_centre(nne_state* s, int target) {
 //    C = (Q^H X)(Q^H X)^H, W = Q * (top-r eigenvectors of C).  Used when
 //    k < n_side; otherwise the sketch spans the space and the exact path runs.
 template <typename R>
-nne_status subspace(nne_state* s, cx<R>* X, int rows, int cols, int r, int dir) {
-  cudaStream_t st = s->ctx->stream;
-  cx<R>* Hm = reinterpret_cast<cx<R>*>(s->H);
-  cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
+nne_status subspace(nne_state* s, const BatchView& b, cx<R>* X, int rows, int cols, int r, int dir) {
+  cudaStream_t st = b.st;
+  cx<R>* Hm = wsb<R>(s->H, s->sH, b);
+  cx<R>* W = wsb<R>(s->U, s->sU, b);
   const cx<R> one = mk<R>(1, 0), zero = mk<R>(0, 0);
   const int n = dir > 0 ? rows : cols;
   const int other = dir > 0 ? cols : rows;
   const int k = s->omega_cols;
   if (s->trunc == NNE_TRUNC_RSVD && s->d_omega && k < n && k >= r) {
     cx<R>* Om = reinterpret_cast<cx<R>*>(s->d_omega);
-    cx<R>* Y = reinterpret_cast<cx<R>*>(s->rs_Y);    // n x k
-    cx<R>* Z = reinterpret_cast<cx<R>*>(s->rs_Z);    // other x k
-    cx<R>* Cm = reinterpret_cast<cx<R>*>(s->rs_C);   // k x k
-    cx<R>* Wk = reinterpret_cast<cx<R>*>(s->rs_W);   // k x r
+    cx<R>* Y = wsb<R>(s->rs_Y, s->rs_sY, b);    // n x k
+    cx<R>* Z = wsb<R>(s->rs_Z, s->rs_sZ, b);    // other x k
+    cx<R>* Cm = wsb<R>(s->rs_C, s->rs_sC, b);   // k x k
+    cx<R>* Wk = wsb<R>(s->rs_W, s->rs_sW, b);   // k x r
     const long long sY = s->rs_sY, sZ = s->rs_sZ, sC = s->rs_sC, sW = s->rs_sW;
     // A = X (dir > 0) or X^H (dir < 0): A is n x other
     const int opA = dir > 0 ? OP_N : OP_C, opAh = dir > 0 ? OP_C : OP_N;
-    CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Om, 0, k, zero, Y, sY, k, s->n_inst));
-    CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, s->qr_ws, s->n_inst));
+    CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Om, 0, k, zero, Y, sY, k, b.nb));
+    CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, qrws<R>(s, b), b.nb));
     // power iterations Y <- A (A^H Q), re-orthonormalised after each application of A A^H
     for (int it = 0; it < s->power_iters; ++it) {
-      CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, s->n_inst));
-      CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Z, sZ, k, zero, Y, sY, k, s->n_inst));
-      CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, s->qr_ws, s->n_inst));
+      CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, b.nb));
+      CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Z, sZ, k, zero, Y, sY, k, b.nb));
+      CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, qrws<R>(s, b), b.nb));
     }
     if (k == r) {   // the sketch space itself is the answer
-      CTRY(copy_batched<R>(st, Y, sY, W, s->sU, (long long)n * k, s->n_inst));
-      CTRY(fix_columns<R>(st, W, s->sU, n, r, s->n_inst));
+      CTRY(copy_batched<R>(st, Y, sY, W, s->sU, (long long)n * k, b.nb));
+      CTRY(fix_columns<R>(st, W, s->sU, n, r, b.nb));
       return NNE_OK;
     }
     // Bt = A^H Q (other x k); C = Bt^H Bt (k x k)
-    CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, s->n_inst));
-    CTRY(cgemm<R>(st, OP_C, OP_N, k, k, other, one, Z, sZ, k, Z, sZ, k, zero, Cm, sC, k, s->n_inst));
-    CTRY(eigh_top<R>(st, Cm, sC, k, r, Wk, sW, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
-    CTRY(cgemm<R>(st, OP_N, OP_N, n, r, k, one, Y, sY, k, Wk, sW, r, zero, W, s->sU, r, s->n_inst));
-    CTRY(fix_columns<R>(st, W, s->sU, n, r, s->n_inst));
+    CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, b.nb));
+    CTRY(cgemm<R>(st, OP_C, OP_N, k, k, other, one, Z, sZ, k, Z, sZ, k, zero, Cm, sC, k, b.nb));
+    CTRY(eigh_top<R>(st, Cm, sC, k, r, Wk, sW, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err));
+    CTRY(cgemm<R>(st, OP_N, OP_N, n, r, k, one, Y, sY, k, Wk, sW, r, zero, W, s->sU, r, b.nb));
+    CTRY(fix_columns<R>(st, W, s->sU, n, r, b.nb));
     return NNE_OK;
   }
   if (dir > 0)
     CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, cols, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, rows,
-                  s->n_inst));
+                  b.nb));
   else
     CTRY(cgemm<R>(st, OP_C, OP_N, cols, cols, rows, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, cols,
-                  s->n_inst));
-  CTRY(eigh_top<R>(st, Hm, s->sH, n, r, W, s->sU, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
-  CTRY(fix_columns<R>(st, W, s->sU, n, r, s->n_inst));
+                  b.nb));
+  CTRY(eigh_top<R>(st, Hm, s->sH, n, r, W, s->sU, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err));
+  CTRY(fix_columns<R>(st, W, s->sU, n, r, b.nb));
   return NNE_OK;
 }
 
 template <typename R>
-nne_status gate_step(nne_state* s, int q, const double* G, long long sG, int dir) {
-  cudaStream_t st = s->ctx->stream;
-  TRY(move_centre<R>(s, dir > 0 ? q : q + 1));
+nne_status gate_compute(nne_state* s, const BatchView& b, int q, const double* G, long long sG, int dir) {
+  cudaStream_t st = b.st;
+  G += 2LL * b.i0 * sG;   // this view's instances
   const int dl = s->dims[q], dm = s->dims[q + 1], dr = s->dims[q + 2];
   const int rows = 4 * dl, cols = 4 * dr;
   const int r = std::min(s->chi, std::min(rows, cols));
-  cx<R>* A = sp<R>(s, q);
-  cx<R>* B = sp<R>(s, q + 1);
-  cx<R>* X = reinterpret_cast<cx<R>*>(s->X);
+  cx<R>* A = spb<R>(s, b, q);
+  cx<R>* B = spb<R>(s, b, q + 1);
+  cx<R>* X = wsb<R>(s->X, s->sX, b);
   // a2: theta = A B ; a3: theta' = G theta
   CTRY(cgemm<R>(st, OP_N, OP_N, rows, cols, dm, mk<R>(1, 0), A, s->sstride[q], dm, B, s->sstride[q + 1], cols,
-                mk<R>(0, 0), X, s->sX, cols, s->n_inst));
-  CTRY(apply_superop<R>(st, X, s->sX, dl, dr, G, sG, s->n_inst));
+                mk<R>(0, 0), X, s->sX, cols, b.nb));
+  CTRY(apply_superop<R>(st, X, s->sX, dl, dr, G, sG, b.nb));
   const long long countX = (long long)rows * cols;
   if (dir > 0) {
     if (r == rows) {
-      CTRY(identity<R>(st, A, s->sstride[q], rows, r, s->n_inst));
-      CTRY(copy_batched<R>(st, X, s->sX, B, s->sstride[q + 1], countX, s->n_inst));
-      TRY(finish_split<R>(s, B, s->sstride[q + 1], countX, nullptr, 0, 0));
+      CTRY(identity<R>(st, A, s->sstride[q], rows, r, b.nb));
+      CTRY(copy_batched<R>(st, X, s->sX, B, s->sstride[q + 1], countX, b.nb));
+      TRY(finish_split<R>(s, b, B, s->sstride[q + 1], countX, nullptr, 0, 0));
     } else if (r == cols) {
       // nothing is cut: X = Q R exactly (Householder), left factor Q, centre R
-      cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
-      CTRY(qr<R>(st, X, s->sX, rows, cols, Q, s->sT, B, s->sstride[q + 1], s->qr_ws, s->n_inst));
-      CTRY(fix_qr<R>(st, Q, s->sT, rows, r, B, s->sstride[q + 1], cols, s->n_inst));
-      CTRY(copy_batched<R>(st, Q, s->sT, A, s->sstride[q], (long long)rows * r, s->n_inst));
-      TRY(finish_split<R>(s, B, s->sstride[q + 1], (long long)r * cols, nullptr, 0, 0));
+      cx<R>* Q = wsb<R>(s->T, s->sT, b);
+      CTRY(qr<R>(st, X, s->sX, rows, cols, Q, s->sT, B, s->sstride[q + 1], qrws<R>(s, b), b.nb));
+      CTRY(fix_qr<R>(st, Q, s->sT, rows, r, B, s->sstride[q + 1], cols, b.nb));
+      CTRY(copy_batched<R>(st, Q, s->sT, A, s->sstride[q], (long long)rows * r, b.nb));
+      TRY(finish_split<R>(s, b, B, s->sstride[q + 1], (long long)r * cols, nullptr, 0, 0));
     } else {
-      TRY(subspace<R>(s, X, rows, cols, r, +1));
-      cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
-      CTRY(copy_batched<R>(st, W, s->sU, A, s->sstride[q], (long long)rows * r, s->n_inst));
+      TRY(subspace<R>(s, b, X, rows, cols, r, +1));
+      cx<R>* W = wsb<R>(s->U, s->sU, b);
+      CTRY(copy_batched<R>(st, W, s->sU, A, s->sstride[q], (long long)rows * r, b.nb));
       CTRY(cgemm<R>(st, OP_C, OP_N, r, cols, rows, mk<R>(1, 0), W, s->sU, r, X, s->sX, cols, mk<R>(0, 0), B,
-                    s->sstride[q + 1], cols, s->n_inst));
-      TRY(finish_split<R>(s, B, s->sstride[q + 1], (long long)r * cols, X, s->sX, countX));
+                    s->sstride[q + 1], cols, b.nb));
+      TRY(finish_split<R>(s, b, B, s->sstride[q + 1], (long long)r * cols, X, s->sX, countX));
     }
-    s->dims[q + 1] = r;
-    s->centre = q + 1;
   } else {
     if (r == cols) {
-      CTRY(identity<R>(st, B, s->sstride[q + 1], r, cols, s->n_inst));
-      CTRY(copy_batched<R>(st, X, s->sX, A, s->sstride[q], countX, s->n_inst));
-      TRY(finish_split<R>(s, A, s->sstride[q], countX, nullptr, 0, 0));
+      CTRY(identity<R>(st, B, s->sstride[q + 1], r, cols, b.nb));
+      CTRY(copy_batched<R>(st, X, s->sX, A, s->sstride[q], countX, b.nb));
+      TRY(finish_split<R>(s, b, A, s->sstride[q], countX, nullptr, 0, 0));
     } else if (r == rows) {
       // nothing is cut: X^H = Q R exactly, right factor Q^H, centre R^H
-      cx<R>* Xh = reinterpret_cast<cx<R>*>(s->H);
-      cx<R>* Q = reinterpret_cast<cx<R>*>(s->T);
-      cx<R>* Rr = reinterpret_cast<cx<R>*>(s->Rm);
-      CTRY(transpose<R>(st, true, X, s->sX, rows, cols, cols, Xh, s->sH, rows, s->n_inst));
-      CTRY(qr<R>(st, Xh, s->sH, cols, rows, Q, s->sT, Rr, s->sR, s->qr_ws, s->n_inst));
-      CTRY(fix_qr<R>(st, Q, s->sT, cols, r, Rr, s->sR, rows, s->n_inst));
-      CTRY(transpose<R>(st, true, Q, s->sT, cols, r, r, B, s->sstride[q + 1], cols, s->n_inst));
-      CTRY(transpose<R>(st, true, Rr, s->sR, r, rows, rows, A, s->sstride[q], r, s->n_inst));
-      TRY(finish_split<R>(s, A, s->sstride[q], (long long)rows * r, nullptr, 0, 0));
+      cx<R>* Xh = wsb<R>(s->H, s->sH, b);
+      cx<R>* Q = wsb<R>(s->T, s->sT, b);
+      cx<R>* Rr = wsb<R>(s->Rm, s->sR, b);
+      CTRY(transpose<R>(st, true, X, s->sX, rows, cols, cols, Xh, s->sH, rows, b.nb));
+      CTRY(qr<R>(st, Xh, s->sH, cols, rows, Q, s->sT, Rr, s->sR, qrws<R>(s, b), b.nb));
+      CTRY(fix_qr<R>(st, Q, s->sT, cols, r, Rr, s->sR, rows, b.nb));
+      CTRY(transpose<R>(st, true, Q, s->sT, cols, r, r, B, s->sstride[q + 1], cols, b.nb));
+      CTRY(transpose<R>(st, true, Rr, s->sR, r, rows, rows, A, s->sstride[q], r, b.nb));
+      TRY(finish_split<R>(s, b, A, s->sstride[q], (long long)rows * r, nullptr, 0, 0));
     } else {
-      TRY(subspace<R>(s, X, rows, cols, r, -1));
-      cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
-      CTRY(transpose<R>(st, true, W, s->sU, cols, r, r, B, s->sstride[q + 1], cols, s->n_inst));
+      TRY(subspace<R>(s, b, X, rows, cols, r, -1));
+      cx<R>* W = wsb<R>(s->U, s->sU, b);
+      CTRY(transpose<R>(st, true, W, s->sU, cols, r, r, B, s->sstride[q + 1], cols, b.nb));
       CTRY(cgemm<R>(st, OP_N, OP_N, rows, r, cols, mk<R>(1, 0), X, s->sX, cols, W, s->sU, r, mk<R>(0, 0), A,
-                    s->sstride[q], r, s->n_inst));
-      TRY(finish_split<R>(s, A, s->sstride[q], (long long)rows * r, X, s->sX, countX));
+                    s->sstride[q], r, b.nb));
+      TRY(finish_split<R>(s, b, A, s->sstride[q], (long long)rows * r, X, s->sX, countX));
     }
-    s->dims[q + 1] = r;
-    s->centre = q;
   }
+  return NNE_OK;
+}
+
+// One gate on every view: centre to the gate, the per-view arithmetic, then
+// the shared bond dimension and centre.
+template <typename R>
+nne_status gate_step(nne_state* s, const std::vector<BatchView>& views, int q, const double* G, long long sG,
+                     int dir) {
+  TRY(move_centre<R>(s, views, dir > 0 ? q : q + 1));
+  const int r = std::min(s->chi, std::min(4 * s->dims[q], 4 * s->dims[q + 2]));
+  for (const BatchView& b : views) TRY(gate_compute<R>(s, b, q, G, sG, dir));
+  s->dims[q + 1] = r;
+  s->centre = dir > 0 ? q + 1 : q;
   return NNE_OK;
 }
 
 template <typename R>
 nne_status compress(nne_state* s, int chi_new) {
-  cudaStream_t st = s->ctx->stream;
-  TRY(move_centre<R>(s, 0));
+  const BatchView b{s->ctx->stream, 0, s->n_inst};
+  const std::vector<BatchView> views{b};
+  cudaStream_t st = b.st;
+  TRY(move_centre<R>(s, views, 0));
   for (int k = 0; k + 1 < s->n; ++k) {
     const int dl = s->dims[k], dr = s->dims[k + 1], dn = s->dims[k + 2];
     const int rows = 4 * dl;
     const int r = std::min(chi_new, std::min(rows, dr));
     if (r >= dr) {
-      TRY(qr_right<R>(s, k));
+      TRY(qr_right<R>(s, b, k));
+      s->dims[k + 1] = std::min(rows, dr);
     } else {
-      cx<R>* M = sp<R>(s, k);
-      cx<R>* Hm = reinterpret_cast<cx<R>*>(s->H);
-      cx<R>* W = reinterpret_cast<cx<R>*>(s->U);
-      cx<R>* Cm = reinterpret_cast<cx<R>*>(s->Rm);
-      cx<R>* Xs = reinterpret_cast<cx<R>*>(s->X);
-      CTRY(copy_batched<R>(st, M, s->sstride[k], Xs, s->sX, (long long)rows * dr, s->n_inst));
+      cx<R>* M = spb<R>(s, b, k);
+      cx<R>* Hm = wsb<R>(s->H, s->sH, b);
+      cx<R>* W = wsb<R>(s->U, s->sU, b);
+      cx<R>* Cm = wsb<R>(s->Rm, s->sR, b);
+      cx<R>* Xs = wsb<R>(s->X, s->sX, b);
+      CTRY(copy_batched<R>(st, M, s->sstride[k], Xs, s->sX, (long long)rows * dr, b.nb));
       CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, dr, mk<R>(1, 0), Xs, s->sX, dr, Xs, s->sX, dr, mk<R>(0, 0), Hm,
-                    s->sH, rows, s->n_inst));
-      CTRY(eigh_top<R>(st, Hm, s->sH, rows, r, W, s->sU, s->eig_cx, s->eig_re, s->eig_u8, s->n_inst, s->d_err));
-      CTRY(fix_columns<R>(st, W, s->sU, rows, r, s->n_inst));
-      CTRY(copy_batched<R>(st, W, s->sU, M, s->sstride[k], (long long)rows * r, s->n_inst));
+                    s->sH, rows, b.nb));
+      CTRY(eigh_top<R>(st, Hm, s->sH, rows, r, W, s->sU, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err));
+      CTRY(fix_columns<R>(st, W, s->sU, rows, r, b.nb));
+      CTRY(copy_batched<R>(st, W, s->sU, M, s->sstride[k], (long long)rows * r, b.nb));
       CTRY(cgemm<R>(st, OP_C, OP_N, r, dr, rows, mk<R>(1, 0), W, s->sU, r, Xs, s->sX, dr, mk<R>(0, 0), Cm, s->sR, dr,
-                    s->n_inst));
-      TRY(finish_split<R>(s, Cm, s->sR, (long long)r * dr, Xs, s->sX, (long long)rows * dr));
-      cx<R>* N = sp<R>(s, k + 1);
-      cx<R>* tmp = reinterpret_cast<cx<R>*>(s->T);
+                    b.nb));
+      TRY(finish_split<R>(s, b, Cm, s->sR, (long long)r * dr, Xs, s->sX, (long long)rows * dr));
+      cx<R>* N = spb<R>(s, b, k + 1);
+      cx<R>* tmp = wsb<R>(s->T, s->sT, b);
       CTRY(cgemm<R>(st, OP_N, OP_N, r, 4 * dn, dr, mk<R>(1, 0), Cm, s->sR, dr, N, s->sstride[k + 1], 4 * dn,
-                    mk<R>(0, 0), tmp, s->sT, 4 * dn, s->n_inst));
-      CTRY(copy_batched<R>(st, tmp, s->sT, N, s->sstride[k + 1], (long long)r * 4 * dn, s->n_inst));
+                    mk<R>(0, 0), tmp, s->sT, 4 * dn, b.nb));
+      CTRY(copy_batched<R>(st, tmp, s->sT, N, s->sstride[k + 1], (long long)r * 4 * dn, b.nb));
       s->dims[k + 1] = r;
     }
     s->centre = k + 1;
@@ -639,10 +705,14 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
   if ((rc = s->mem.alloc(&s->Rm, (size_t)s->sR * n_inst * s->esz)) != NNE_OK) return fail(rc);
   const EighWork ew = eigh_workspace((int)N4, (int)D);
   const size_t rsz = s->esz / 2;
+  s->eig_cx_pi = ew.cx_elems;
+  s->eig_re_pi = ew.re_elems;
+  s->eig_u8_pi = ew.u8_elems;
   if ((rc = s->mem.alloc(&s->eig_cx, (size_t)ew.cx_elems * n_inst * s->esz)) != NNE_OK) return fail(rc);
   if ((rc = s->mem.alloc(&s->eig_re, (size_t)ew.re_elems * n_inst * rsz + 256)) != NNE_OK) return fail(rc);
   if ((rc = s->mem.alloc(&s->eig_u8, (size_t)ew.u8_elems * n_inst)) != NNE_OK) return fail(rc);
   const QrWork qw = qr_workspace((int)N4, (int)N4);
+  s->qr_pi = qw.cx_elems;
   if ((rc = s->mem.alloc(&s->qr_ws, (size_t)qw.cx_elems * n_inst * s->esz)) != NNE_OK) return fail(rc);
   s->bits.assign(n, 0);
   if (init_bits)
@@ -670,6 +740,25 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return fail(set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__));
   }
+  // concurrent sub-batches of the gate steps (streams and fork/join events); only where the
+  // kernels are large (bonds of 256 and more): small states are launch-bound, and splitting
+  // them multiplies their launches
+  s->nsub = s->dmax >= 256 ? std::max(1, std::min(g_substreams, n_inst)) : 1;
+  if (s->nsub > 1) {
+    cudaError_t e2 = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    for (int v = 0; v < s->nsub && e2 == cudaSuccess; ++v) {
+      cudaStream_t q = nullptr;
+      cudaEvent_t ev = nullptr;
+      e2 = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+      if (e2 == cudaSuccess) s->sub_st.push_back(q);
+      if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e2 == cudaSuccess) s->ev_join.push_back(ev);
+    }
+    if (e2 != cudaSuccess) {
+      destroy_streams(s);
+      return fail(set_cuda_error(e2, "sub-batch streams", __FILE__, __LINE__));
+    }
+  }
   *out = s;
   return NNE_OK;
 }
@@ -678,6 +767,8 @@ void nne_destroy_state(nne_state* st) {
   if (!st) return;
   DeviceGuard g(st->ctx->device);
   cudaStreamSynchronize(st->ctx->stream);
+  for (cudaStream_t q : st->sub_st) cudaStreamSynchronize(q);
+  destroy_streams(st);
   st->mem.release();
   delete st;
 }
@@ -719,12 +810,27 @@ nne_status nne_apply_layer(nne_state* st, int n_gates, const int* left_qubit, co
   DeviceGuard dg(st->ctx->device);
   const double* Gd = reinterpret_cast<const double*>(G);
   const long long sG = (long long)n_gates * 256;   // complex elements between instances
-  for (int g = 0; g < n_gates; ++g) {
-    nne_status rc = st->dtype == NNE_C64 ? gate_step<float>(st, left_qubit[g], Gd + 2LL * 256 * g, sG, direction)
-                                         : gate_step<double>(st, left_qubit[g], Gd + 2LL * 256 * g, sG, direction);
-    if (rc != NNE_OK) return rc;
+  // the instances split into nsub views, each on its own stream, forked from and joined back
+  // to the context stream; gate by gate the host enqueues every view's work in turn
+  std::vector<BatchView> views;
+  for (int v = 0; v < st->nsub; ++v) {
+    const int i0 = (int)((long long)st->n_inst * v / st->nsub), i1 = (int)((long long)st->n_inst * (v + 1) / st->nsub);
+    views.push_back(BatchView{st->nsub > 1 ? st->sub_st[v] : st->ctx->stream, i0, i1 - i0});
   }
-  return NNE_OK;
+  if (st->nsub > 1) {
+    NNE_CUDA_TRY(cudaEventRecord(st->ev_fork, st->ctx->stream));
+    for (int v = 0; v < st->nsub; ++v) NNE_CUDA_TRY(cudaStreamWaitEvent(st->sub_st[v], st->ev_fork, 0));
+  }
+  nne_status rc = NNE_OK;
+  for (int g = 0; g < n_gates && rc == NNE_OK; ++g)
+    rc = st->dtype == NNE_C64 ? gate_step<float>(st, views, left_qubit[g], Gd + 2LL * 256 * g, sG, direction)
+                              : gate_step<double>(st, views, left_qubit[g], Gd + 2LL * 256 * g, sG, direction);
+  if (st->nsub > 1)
+    for (int v = 0; v < st->nsub; ++v) {
+      cudaEventRecord(st->ev_join[v], st->sub_st[v]);
+      cudaStreamWaitEvent(st->ctx->stream, st->ev_join[v], 0);
+    }
+  return rc;
 }
 
 nne_status nne_truncate(nne_state* st, int chi_new, double* log_fid_out) {
@@ -905,6 +1011,7 @@ nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits) {
 
 void nne_set_option(int option, int value) {
   if (option == NNE_OPT_TENSOR_CORES) set_tensor_cores(value);
+  if (option == NNE_OPT_SUBBATCHES) g_substreams = value < 1 ? 1 : (value > 8 ? 8 : value);
 }
 
 nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, const float* alpha, const void* A,

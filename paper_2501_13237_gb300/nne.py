@@ -250,6 +250,7 @@ def set_option(option: int, value: int):
 
 
 OPT_TENSOR_CORES = 0
+OPT_SUBBATCHES = 1
 
 
 class State:
