@@ -169,7 +169,7 @@ def main():
 
     import torch
     import workloads as wl
-    from paper_2501_13237_gb300 import nne, runner
+    from paper_2501_13237_gb300 import nne, replicas, runner
 
     torch.cuda.set_device(local)
     dist = None
@@ -177,7 +177,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
 
-    w = wl.n100(seed=rank)
+    w = wl.n100(seed=replicas.replica_seed(rank))
     rates = w.rate_table()
     n_inst = rates.shape[0]
     paulis = wl.pauli_codes(w.observables, w.n)
@@ -261,25 +261,23 @@ def main():
             nne.prof_enable(False)
             pr = nne.prof_collect()
         ms = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, launches, pr
+        # slowest rank's time, every rank's gate steps
+        ms, units = replicas.aggregate(ms, gates_per_step * K, dist, dev)
+        return ms, launches, pr, units
 
     for _ in range(args.warmup):
         step(False)
     clocks = ClockSampler(local)
     clocks.start()
-    ms, launches, _ = timed(False, args.steps)
+    ms, launches, _, units = timed(False, args.steps)
     clk = clocks.stop()
-    ms_e2e, _, _ = timed(True, 1)
+    ms_e2e, _, _, units_e2e = timed(True, 1)
     # per-kernel-class breakdown from a separate profiled step (event pairs around
     # every launch add host work, so the headline is timed without them)
-    ms_prof, _, prof = timed(False, 1, prof=True)
+    ms_prof, _, prof, _ = timed(False, 1, prof=True)
 
-    value = gates_per_step * args.steps * world / (ms / 1e3)
-    e2e = gates_per_step * world / (ms_e2e / 1e3)
+    value = units / (ms / 1e3)
+    e2e = units_e2e / (ms_e2e / 1e3)
 
     # roofline for the dominant kernel class
     pk = peaks()
@@ -365,7 +363,7 @@ def serving_run(n_requests: int, rate_per_s: float, seed: int, workers: int, dev
     depth in [5, 20], chi in {16, 32, 64, 128}, 4-8 levels, random channel mix,
     all <Z_i>, complex64, exact truncation).  Latency = completion - arrival."""
     import workloads as wl
-    from paper_2501_13237_gb300 import nne, runner
+    from paper_2501_13237_gb300 import nne, replicas, runner
     reqs = wl.serving_stream(seed, n_requests, rate_per_s, n_range=(8, 32), depth_range=(5, 20),
                              chis=(16, 32, 64, 128))
     jobs = [runner.job_for(r.workload, dtype=nne.C64) for r in reqs]

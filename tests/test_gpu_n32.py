@@ -1,0 +1,61 @@
+"""The n=32 workload (depth 20, chi=128, six levels of depolarizing plus
+amplitude damping, all <Z_i>): the complex64 path at full size next to the
+complex128 path, and its first eight layers against the oracle MPS."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from gpu_util import require_gpu
+from oracle import mps
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    from paper_2501_13237_gb300 import nne
+    return nne.Context(0)
+
+
+def test_n32_complex64_next_to_complex128(ctx):
+    from paper_2501_13237_gb300 import runner
+    w = wl.n32()
+    rates = w.rate_table()
+    paulis = wl.pauli_codes(w.observables, w.n)
+    st, v64, lf64 = runner.emulate(ctx, w.circuit, rates, w.chi, paulis, 0, bits=w.bits())
+    st.close()
+    st, v128, lf128 = runner.emulate(ctx, w.circuit, rates, w.chi, paulis, 1, bits=w.bits())
+    st.close()
+    assert (lf128 < -1e-4).all()                       # truncation happens
+    # same truncations up to float32 rounding of the Gram eigenproblem
+    assert np.abs(v64.real - v128.real).max() < 1e-3
+    assert np.abs(lf64 - lf128).max() < 1e-3 * np.abs(lf128).max()
+
+
+_ORACLE = {}
+
+
+def _prefix():
+    w = wl.n32()
+    c = dataclasses.replace(w.circuit, depth=8, layers=w.circuit.layers[:8], unitaries=w.circuit.unitaries[:8])
+    rates = w.rate_table()[[0, 5]]
+    if not _ORACLE:
+        _ORACLE["refs"] = [mps.run(c, rates[i], w.chi, bits=w.bits()) for i in range(2)]
+    return w, c, rates, _ORACLE["refs"]
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 3e-4)])
+def test_n32_prefix_vs_oracle(ctx, dtype, tol):
+    from paper_2501_13237_gb300 import runner
+    w, c, rates, refs = _prefix()
+    paulis = wl.pauli_codes(w.observables, w.n)
+    st, vals, lf = runner.emulate(ctx, c, rates, w.chi, paulis, dtype, bits=w.bits())
+    st.close()
+    for i in range(2):
+        ref = refs[i]
+        assert ref.log_fid < -1e-6                     # chi = 128 cuts at depth 8
+        assert np.abs(vals[i].real - ref.expect_codes(paulis).real).max() < tol
+        assert abs(lf[i] - ref.log_fid) < tol * max(1.0, abs(ref.log_fid)) * 10
