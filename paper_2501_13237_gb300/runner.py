@@ -78,3 +78,26 @@ def emulate_ladder(ctx: nne.Context, circuit, rates: np.ndarray, chis, paulis: n
         vals.append(v.real)
         lfs.append(lf)
     return np.stack(vals), np.stack(lfs)
+
+
+def nzne(ctx: nne.Context, circuit, noise, lambdas, chis, paulis: np.ndarray, lambda_star: float = 1.0,
+         method: int = nne.FIT_EXP_LOGLIN, degree: int = 2, dtype: int = nne.C64, with_zero: bool = True, bits=None):
+    """The paper's pipeline for one circuit: emulations at every level of
+    `lambdas` (and at lambda = 0, noise free, when with_zero) for each bond
+    dimension of the ladder `chis`, fidelity extrapolation and criterion 1
+    (A), then extrapolation in the noise strength to lambda* (B).  The
+    lambda = 0 emulation at the largest chi is the sign reference of
+    criterion 3 and does not enter the fit.  `noise` is a workloads.NoiseModel
+    (strengths scaled by lambda)."""
+    lam = np.asarray(lambdas, np.float64)
+    levels = ([0.0] if with_zero else []) + list(lam)
+    rates = np.stack([noise.rates(l) for l in levels])
+    vals, lfs = emulate_ladder(ctx, circuit, rates, chis, paulis, dtype, bits=bits)
+    y_zero = None
+    if with_zero:
+        y_zero = vals[-1, 0].copy()
+        vals, lfs = vals[:, 1:], lfs[:, 1:]
+    est, status, obar, conv = ctx.extrapolate_ladder(lam, vals, lfs, method=method, degree=degree,
+                                                     lambda_star=lambda_star, y_zero=y_zero)
+    return {"estimate": est, "status": status, "obar": obar, "converged": conv, "values": vals, "log_fid": lfs,
+            "y_zero": y_zero}

@@ -79,3 +79,32 @@ def test_chi_ladder_emulation_vs_oracle(ctx, dtype, tol):
     assert agree.mean() > 0.95                 # criterion 1 may flip only at its threshold
     ok = (st == 0) & (rst == 0) & agree.all(axis=0)
     assert np.abs(est[ok] - rest[ok]).max() < 100 * tol
+
+
+def test_full_pipeline_with_noise_free_reference(ctx):
+    """lambda = 0 emulated next to the noisy levels (rates zero) gives the
+    sign reference of criterion 3; the whole pipeline matches the oracle's."""
+    from paper_2501_13237_gb300 import runner
+    n, chis = 8, (16, 32, 64)
+    c = wl.brickwork_circuit(n, 8, 12)
+    noise = wl.NoiseModel(depol2=0.01, amp_damp=0.005, dephase=0.005)
+    lams = np.array([1.0, 2.0, 3.0, 4.0])
+    obs = wl.obs_z(n) + wl.obs_zz(n)
+    paulis = wl.pauli_codes(obs, n)
+    res = runner.nzne(ctx, c, noise, lams, chis, paulis, lambda_star=1.0, dtype=1)
+    rv = np.zeros((len(chis), len(lams), len(obs)))
+    rl = np.zeros((len(chis), len(lams)))
+    for j, chi in enumerate(chis):
+        for i, lam in enumerate(lams):
+            st = mps.run(c, noise.rates(lam), chi)
+            rv[j, i] = st.expect_codes(paulis).real
+            rl[j, i] = st.log_fid
+    y0 = mps.run(c, noise.rates(0.0), chis[-1]).expect_codes(paulis).real
+    assert np.abs(res["y_zero"] - y0).max() < 1e-8
+    est, st, ob, cv = fit.nzne(1, lams, rv, rl, 1.0, y_zero=y0)
+    assert np.array_equal(res["converged"], cv)
+    assert np.array_equal(res["status"], st)
+    ok = st == 0
+    assert np.abs(res["estimate"][ok] - est[ok]).max() < 1e-6
+    # the pure-state reference decides criterion 3 for observables whose sign changes along lambda
+    assert np.isfinite(res["estimate"][ok]).all()
