@@ -6,7 +6,7 @@ rho_0 = |b><b| a computational basis product state.  No approximation: this
 is the exact target the VMPO emulation approximates, and the true fidelity
 F of eq. (true_fidelity) is computed against it.
 
-Pins (tests/test_oracle_dense.py): trace preservation, Hermiticity, closed
+Pins (tests/test_oracle_dense.py, tests/test_oracle_entropy.py): trace preservation, Hermiticity, closed
 forms for identity circuits under each channel, agreement with the
 statevector simulator at zero noise.
 """
@@ -79,3 +79,19 @@ def true_fidelity(rho_approx: np.ndarray, rho_exact: np.ndarray) -> float:
     ip = np.vdot(rho_approx.ravel(), rho_exact.ravel())
     return float(abs(ip) ** 2 / (np.vdot(rho_approx.ravel(), rho_approx.ravel()).real
                                  * np.vdot(rho_exact.ravel(), rho_exact.ravel()).real))
+
+
+def mpo_entropy(rho: np.ndarray, l: int, n: int) -> float:
+    """MPO entanglement entropy of vec(rho) across the cut after qubit l (App. A.1).
+
+    The definition itself: write vec(rho) with site index s = 2 i + j for the
+    ket / bra bits (i, j) of each qubit, reshape it into a matrix from the
+    first l sites to the last n - l, and take the Shannon entropy of its
+    normalised squared singular values."""
+    T = np.asarray(rho).reshape([2] * (2 * n))                 # kets i_0..i_{n-1}, then bras j_0..j_{n-1}
+    perm = [a for k in range(n) for a in (k, n + k)]           # (i_0, j_0, i_1, j_1, ...)
+    V = T.transpose(perm).reshape(4 ** l, 4 ** (n - l))
+    s = np.linalg.svd(V, compute_uv=False)
+    w = s ** 2
+    p = w[w > 0.0] / np.sum(w)
+    return float(-np.sum(p * np.log(p)))

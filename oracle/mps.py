@@ -207,6 +207,39 @@ class VMPO:
     def bond_dims(self) -> List[int]:
         return [m.shape[2] for m in self.M[:-1]]
 
+    # ------------------------------------------------------------- entanglement
+    def mpo_entropies(self) -> np.ndarray:
+        """MPO entanglement entropy S_l for every bond l = 1..n-1 (App. A.1).
+
+        S_l = -sum_i p_i ln p_i with p_i = s_i^2 / sum_j s_j^2, s_i the Schmidt
+        coefficients of |rho>> across the cut after qubit l.  In canonical form
+        with the centre on site k (App. A.1 footnote) they are the singular
+        values of M[k] as a (4 chi_l) x chi_r matrix, for the bond right of k:
+        move the centre to site 0, then take the SVD of each site and move on
+        by QR.  Leaves the centre at site n-1; the state is unchanged."""
+        self.move_centre(0)
+        out = np.zeros(self.n - 1)
+        for k in range(self.n - 1):
+            A = self.M[k]
+            s = np.linalg.svd(A.reshape(A.shape[0] * 4, A.shape[2]), compute_uv=False)
+            out[k] = entropy_of_schmidt(s)
+            self.move_centre(k + 1)
+        return out
+
+    def s_max(self) -> float:
+        """S_max = max over bonds of S_l (App. A.1); 0 for a single site."""
+        return float(np.max(self.mpo_entropies())) if self.n > 1 else 0.0
+
+
+def entropy_of_schmidt(s: np.ndarray) -> float:
+    """-sum p ln p over p_i = s_i^2 / sum s^2 (App. A.1), with 0 ln 0 = 0."""
+    w = np.asarray(s, dtype=float) ** 2
+    t = float(np.sum(w))
+    if t <= 0.0:
+        return 0.0
+    p = w[w > 0.0] / t
+    return float(-np.sum(p * np.log(p)))
+
 
 def theta_superop(A: np.ndarray, B: np.ndarray, G: np.ndarray) -> np.ndarray:
     """X = (G . theta) as a (4 chi_l) x (4 chi_r) matrix, rows (a, s1'), cols (s2', b)."""
