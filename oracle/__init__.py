@@ -10,13 +10,16 @@ the two sides have in common is the seeded input generator in
 
 Modules
   channels    -- Kraus sets and 16x16 gate+channel superoperators
-                 (Sec. 2.2.1 eq. U -> C o U; App. C.2.1)
+                 (Sec. 2.2.1 eq. U -> C o U; App. C.2.1), gate-dependent
+                 Pauli channels (cat-qubit App. C.2.2, matchgate App. C.3.1)
   dense       -- exact density-matrix simulator for n <= 10
   statevector -- pure-state simulator (lambda = 0 reference)
   mps         -- vectorised-MPO (VMPO) emulator: theta formation, superoperator,
                  SVD truncation to fixed D, Frobenius normalisation, partial
                  fidelities (Sec. 2.1.1-2.1.2, eqs. for f_l and F), centre moves,
                  Pauli expectation values
+  matchgate   -- exact noisy expectation values of matchgate circuits under
+                 Pauli noise (free-fermion covariance evolution; App. C.3)
   fit         -- noise extrapolation: polynomial, weighted log-linear and
                  three-parameter exponential fits with criteria 2-3
                  (Sec. 2.2.3 (B), App. B.2)

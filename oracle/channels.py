@@ -23,6 +23,10 @@ channel C; here C is the composition, in this order, of
 The order of 2-4 is a reading (the paper never composes channels); it is
 stated in DESIGN.md.
 
+Gate-dependent Pauli channels (cat-qubit noise, App. C.2.2; matchgate
+depolarizing noise, App. C.3.1) are built by kraus_pauli from 16
+probabilities per gate.
+
 Pins (tests/test_oracle_channels.py): Kraus completeness; the closed-form maps
 of App. C.2.1 and of the single-qubit channels applied to random density
 matrices by explicit K rho K^dagger products; unitality; agreement of the
@@ -106,6 +110,30 @@ def noise_superop(rates) -> np.ndarray:
 def gate_superop(U: np.ndarray, rates) -> np.ndarray:
     """G = S_C . S_U, the fused gate+channel superoperator (eq. U -> C o U)."""
     return noise_superop(rates) @ superop([U])
+
+
+def kraus_pauli(probs) -> list:
+    """Pauli channel on two qubits: K_ab = sqrt(p_ab) sigma_a (x) sigma_b, p_ab =
+    probs[4a+b] (a on the left qubit).  The two-qubit depolarizing channel of
+    App. C.2.1, the cat-qubit errors of App. C.2.2 and the matchgate
+    depolarizing channel of App. C.3.1 are all of this form."""
+    p = np.asarray(probs, dtype=float)
+    if p.shape != (16,) or (p < -1e-15).any():
+        raise ValueError("need 16 non-negative probabilities")
+    return [np.sqrt(max(p[4 * a + b], 0.0)) * np.kron(PAULI[a], PAULI[b])
+            for a in range(4) for b in range(4) if p[4 * a + b] > 0.0]
+
+
+def pauli_gate_superop(U: np.ndarray, probs) -> np.ndarray:
+    """G = S_P . S_U: the gate followed by its Pauli channel (eq. U -> C o U)."""
+    return superop(kraus_pauli(probs)) @ superop([U])
+
+
+def pauli_superops_for(pc, lam: float) -> list:
+    """Per layer of a Pauli-noise circuit: (blocks, 16, 16) superoperators at level lam."""
+    return [np.stack([pauli_gate_superop(U, pr) for U, pr in zip(us, pc.probs(t, lam))])
+            if len(us) else np.zeros((0, 16, 16), complex)
+            for t, us in enumerate(pc.unitaries)]
 
 
 def apply_kraus_dense(rho: np.ndarray, kraus) -> np.ndarray:

@@ -58,6 +58,19 @@ def run(circuit, rates, bits=None) -> np.ndarray:
     return rho
 
 
+def run_pauli(pc, lam: float, bits=None) -> np.ndarray:
+    """Final density matrix of a Pauli-noise circuit at level lam: each block
+    rho <- sum_K K U rho U^dagger K^dagger with the block's Pauli Kraus set."""
+    n = pc.n
+    rho = basis_state(bits if bits is not None else [0] * n)
+    for t, (qs, us) in enumerate(zip(pc.layers, pc.unitaries)):
+        for q, U, pr in zip(qs, us, pc.probs(t, lam)):
+            Ue = embed(U, q, n)
+            rho = Ue @ rho @ Ue.conj().T
+            rho = channels.apply_kraus_dense(rho, [embed(K, q, n) for K in channels.kraus_pauli(pr)])
+    return rho
+
+
 def pauli_matrix(ob, n: int) -> np.ndarray:
     """Pauli string given as ((qubit, 'X'|'Y'|'Z'), ...) as a 2^n x 2^n matrix."""
     ops = ["I"] * n

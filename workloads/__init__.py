@@ -212,6 +212,146 @@ def serving_stream(seed: int = 0, n_requests: int = 2000, rate_per_s: float = 20
     return out
 
 
+# ---------------------------------------------------------------- Pauli-noise circuits
+# Gate-dependent Pauli noise: after each gate on (q, q+1) the Pauli sigma_a (x)
+# sigma_b (a on q, b on q+1; 0=I 1=X 2=Y 3=Z) is applied with probability
+# c0[4a+b] + lambda * c1[4a+b].  The tables below are the paper's noise models,
+# written as data.
+
+# Cat-qubit noise (App. C.2.2, Table): errors per gate at strength lambda, as
+# (probability at lambda = 0, coefficient of lambda) per error.
+CAT_TABLE = {
+    "Z_theta": {"I": (1.0, -1.0), "Z": (0.0, 1.0)},
+    "H": {"I": (1.0, -5.0), "Z": (0.0, 3.0), "X": (0.0, 2.0)},
+    "CX": {"I": (1.0, -4.0), "Z1": (0.0, 3.0), "Z2": (0.0, 0.5), "Z1Z2": (0.0, 0.5)},
+}
+
+# Matchgate depolarizing channel (App. C.3.1): I with 1 - lambda, each of
+# ZI, IZ, XX, XY, YY, YX, ZZ with lambda / 7 (first letter on qubit q).
+MATCHGATE_PAULIS = ("ZI", "IZ", "XX", "XY", "YY", "YX", "ZZ")
+
+_PIDX = {"I": 0, "X": 1, "Y": 2, "Z": 3}
+
+
+def pauli_index(left: str, right: str) -> int:
+    return 4 * _PIDX[left] + _PIDX[right]
+
+
+@dataclasses.dataclass
+class PauliCircuit:
+    """Two-qubit blocks on (q, q+1), each a unitary followed by a Pauli channel
+    whose probabilities are linear in lambda (c0 + lambda c1, 16 per block)."""
+    n: int
+    name: str
+    layers: List[List[int]]          # left qubit per block, per layer
+    unitaries: List[np.ndarray]      # per layer: (blocks, 4, 4) complex128
+    c0: List[np.ndarray]             # per layer: (blocks, 16) float64
+    c1: List[np.ndarray]             # per layer: (blocks, 16) float64
+
+    @property
+    def n_gates(self) -> int:
+        return sum(len(l) for l in self.layers)
+
+    def probs(self, layer: int, lam: float) -> np.ndarray:
+        return self.c0[layer] + lam * self.c1[layer]
+
+
+def _embed_1q(u2: np.ndarray, on_left: bool) -> np.ndarray:
+    return np.kron(u2, np.eye(2)) if on_left else np.kron(np.eye(2), u2)
+
+
+_H2 = np.array([[1, 1], [1, -1]], complex) / np.sqrt(2.0)
+# CX with the control on the more significant (left) qubit, and on the right one
+_CX_L = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], complex)
+_CX_R = np.array([[1, 0, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0], [0, 1, 0, 0]], complex)
+
+
+def cat_gate_noise(gate: str, on_left: bool) -> Tuple[np.ndarray, np.ndarray]:
+    """(c0, c1) over the 16 two-qubit Paulis for one gate of the cat-qubit
+    model; on_left: the single-qubit gate, or the CX control, is on qubit q."""
+    c0, c1 = np.zeros(16), np.zeros(16)
+    for err, (a0, a1) in CAT_TABLE[gate].items():
+        if err == "I":
+            k = 0
+        elif gate == "CX":
+            ctrl, targ = ("Z", "I") if err == "Z1" else (("I", "Z") if err == "Z2" else ("Z", "Z"))
+            k = pauli_index(ctrl, targ) if on_left else pauli_index(targ, ctrl)
+        else:
+            k = pauli_index(err, "I") if on_left else pauli_index("I", err)
+        c0[k] += a0
+        c1[k] += a1
+    return c0, c1
+
+
+def cat_circuit(n: int, depth: int, seed: int) -> PauliCircuit:
+    """Random H / CX / Z(theta) circuit under cat-qubit noise: brickwork pairs,
+    each block one gate drawn uniformly from {CX, H, Z(theta)}; the CX control,
+    and the qubit of a single-qubit gate, is left or right with probability
+    1/2; theta ~ U[0, 2 pi).  Single-qubit gates and their noise are embedded
+    in the pair's 4x4 space."""
+    rng = np.random.default_rng(seed)
+    layers = brickwork_pairs(n, depth)
+    us, c0s, c1s = [], [], []
+    for qs in layers:
+        u, a, b = [], [], []
+        for _ in qs:
+            kind = int(rng.integers(0, 3))
+            left = bool(rng.integers(0, 2))
+            if kind == 0:
+                U, g = (_CX_L if left else _CX_R), "CX"
+            elif kind == 1:
+                U, g = _embed_1q(_H2, left), "H"
+            else:
+                th = float(rng.uniform(0.0, 2.0 * np.pi))
+                U, g = _embed_1q(np.diag([np.exp(-0.5j * th), np.exp(0.5j * th)]), left), "Z_theta"
+            x0, x1 = cat_gate_noise(g, left)
+            u.append(U)
+            a.append(x0)
+            b.append(x1)
+        us.append(np.stack(u) if u else np.zeros((0, 4, 4), complex))
+        c0s.append(np.stack(a) if a else np.zeros((0, 16)))
+        c1s.append(np.stack(b) if b else np.zeros((0, 16)))
+    return PauliCircuit(n, f"cat_n{n}_d{depth}_s{seed}", layers, us, c0s, c1s)
+
+
+def xym_circuit(n: int = 60, steps: int = 30, J: float = 0.5, h: float = 0.23, dt: float = 0.1) -> PauliCircuit:
+    """Trotterised XY-model evolution (App. C.1.3) under matchgate depolarizing
+    noise: each step is a layer of gates on the even bonds (0,1), (2,3), ...
+    followed by a layer on the odd bonds, 59 two-qubit gates per step for
+    n = 60 (1770 over 30 steps).  Bond gate exp(-i dt J (XX + YY)); the field
+    exp(-i dt h Z) of every qubit is carried by its even-bond gate (n even),
+    which is exact because XX + YY commutes with Z (x) I + I (x) Z."""
+    XX = np.kron([[0, 1], [1, 0]], [[0, 1], [1, 0]]).astype(complex)
+    YY = np.kron([[0, -1j], [1j, 0]], [[0, -1j], [1j, 0]])
+    ZI = np.kron(np.diag([1.0, -1.0]), np.eye(2)).astype(complex)
+    IZ = np.kron(np.eye(2), np.diag([1.0, -1.0])).astype(complex)
+
+    def expi(Hm):   # exp(-i dt Hm) of a Hermitian 4x4
+        w, V = np.linalg.eigh(Hm)
+        return (V * np.exp(-1j * dt * w)[None, :]) @ V.conj().T
+
+    U_even = expi(J * (XX + YY) + h * (ZI + IZ))
+    U_odd = expi(J * (XX + YY))
+    c0, c1 = np.zeros(16), np.zeros(16)
+    c0[0], c1[0] = 1.0, -1.0
+    for p in MATCHGATE_PAULIS:
+        c1[pauli_index(p[0], p[1])] += 1.0 / 7.0
+    layers, us, c0s, c1s = [], [], [], []
+    for _ in range(steps):
+        for par, U in ((0, U_even), (1, U_odd)):
+            qs = list(range(par, n - 1, 2))
+            layers.append(qs)
+            us.append(np.stack([U] * len(qs)))
+            c0s.append(np.tile(c0, (len(qs), 1)))
+            c1s.append(np.tile(c1, (len(qs), 1)))
+    return PauliCircuit(n, f"xym_n{n}_steps{steps}", layers, us, c0s, c1s)
+
+
+def neel_bits(n: int) -> np.ndarray:
+    """|1010...>: qubit 0 in |1>, alternating (App. C.1.3 initial state)."""
+    return np.array([(k + 1) % 2 for k in range(n)], np.uint8)
+
+
 def gaussian_sketch(rows: int, cols: int, seed: int) -> np.ndarray:
     """Complex Gaussian test matrix (rows x cols), unit variance per entry."""
     rng = np.random.default_rng(seed)
