@@ -104,6 +104,24 @@ const char* nne_last_error(void);
 nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_inst,
                               const double* rates, void* G_out);
 
+/* a1 for gate-dependent Pauli noise (cat-qubit errors, App. C.2.2; matchgate
+ * depolarizing noise, App. C.3.1; two-qubit depolarizing, App. C.2.1, is the
+ * case p_ab = lambda/16): G[i][g] = S_P (U_g (x) conj(U_g)) with
+ * S_P = sum_ab p_ab K_ab (x) conj(K_ab), K_ab = sigma_a (x) sigma_b (a on the
+ * left qubit q, b on q+1; 0 = I, 1 = X, 2 = Y, 3 = Z) and
+ * p_ab = c0[g][4a+b] + lambdas[i] * c1[g][4a+b].
+ * U           n_gates x 4 x 4 complex128 (as nne_build_superops);
+ * pauli_rates n_gates x 2 x 16 doubles: c0 then c1 of each gate;
+ * lambdas     n_inst doubles;
+ * all three in host or device memory (detected).  With host pauli_rates and
+ * lambdas every p_ab must lie in [0, 1] and each gate's 16 sum to 1 within
+ * 1e-12, else NNE_ERR_ARG; device inputs are not checked.
+ * G_out device, n_inst x n_gates x 256 complex128.  Float64 on the device;
+ * synchronises the context stream when inputs are staged from the host. */
+nne_status nne_build_pauli_superops(nne_ctx* ctx, int n_gates, const double* U,
+                                    const double* pauli_rates, int n_inst,
+                                    const double* lambdas, void* G_out);
+
 /* State creation: n_inst instances of the product state |b><b| (Sec. 2.1.2:
  * the initial state is a product state), bond dimensions 1, orthogonality
  * centre on site 0, log-norm and log-fidelity 0.
@@ -146,6 +164,25 @@ nne_status nne_truncate(nne_state* st, int chi_new, double* log_fid_out);
  * (log F of each instance).  Synchronises the context stream. */
 nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* re_out,
                       double* im_out, double* log_fid_out);
+
+/* MPO entanglement entropy of every bond (App. A.1): S_l = -sum_i p_i ln p_i
+ * with p_i = s_i^2 / sum_j s_j^2 over the Schmidt values s_i of the state
+ * across the cut after qubit l, for l = 1 .. n-1.  Computed by a canonical
+ * sweep: the centre moves to site 0, then right one site at a time (QR); at
+ * site k the squared Schmidt values of the bond k | k+1 are the eigenvalues of
+ * the centre tensor's Gram matrix, found by tridiagonalisation and bisection
+ * in the state's precision, and S is summed in FP64.  The state itself is
+ * unchanged; its centre ends on site n-1.  S_max (App. A.1) is the maximum of
+ * a row.
+ *   S_out host double n_inst x (n-1), row-major: S_out[i * (n-1) + k] is the
+ *         entropy of instance i at the bond between qubits k and k+1.
+ * The Gram matrices are formed in the state's precision, so squared Schmidt
+ * values below about machine epsilon times the largest are not resolved
+ * (complex64: ~1e-7), and a state written with nne_state_write_site must
+ * keep its squared norm inside that precision's range (evolved states have
+ * norm 1).  Synchronises the context stream; returns NNE_ERR_ARG for a null
+ * argument, NNE_ERR_CUDA on a CUDA failure. */
+nne_status nne_entropy(nne_state* st, double* S_out);
 
 /* a8 -- noise extrapolation to lambda_star (Sec. 2.2.3 (B), App. B.2), FP64
  * on the device, one thread per observable.

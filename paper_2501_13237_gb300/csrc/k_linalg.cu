@@ -366,6 +366,27 @@ __global__ void inviter_kernel(const R* db, const R* eb, int n, int r, int ldde,
   }
 }
 
+// S[z] = -sum_i p_i ln p_i, p_i = max(lam_i, 0) / sum_j max(lam_j, 0), over the
+// n eigenvalues of a Gram matrix (the squared Schmidt values of a bond,
+// App. A.1).  One block per matrix, FP64 sums in a fixed order; rounding can
+// leave tiny negative eigenvalues, which count as zero.
+template <typename R>
+__global__ void __launch_bounds__(256) entropy_kernel(const R* lamb, int n, int ldl, double* S, long long sS) {
+  __shared__ double red[8];
+  const R* lam = lamb + (long long)blockIdx.x * ldl;
+  double t = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t += fmax((double)lam[i], 0.0);
+  const double tot = block_sum(t, red);
+  double h = 0;
+  if (tot > 0)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double p = fmax((double)lam[i], 0.0) / tot;
+      if (p > 0) h -= p * log(p);
+    }
+  h = block_sum(h, red);
+  if (threadIdx.x == 0) S[(long long)blockIdx.x * sS] = h;
+}
+
 // ---------------------------------------------------------------- launchers
 template <typename K, typename... Args>
 static cudaError_t launch_cluster(K kernel, int cs, int batch, size_t smem, cudaStream_t st, Args... args) {
@@ -466,9 +487,53 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
   return qr<R>(st, U, sU, n, r, U, sU, nullptr, 0, qrws, batch);
 }
 
+template <typename R>
+cudaError_t gram_entropy(cudaStream_t st, cx<R>* H, long long sH, int n, void* cx_ws, void* re_ws, int batch,
+                         double* S, long long sS) {
+  if (batch <= 0) return cudaSuccess;
+  if (n <= 1) return cudaMemset2DAsync(S, sizeof(double) * sS, 0, sizeof(double), batch, st);
+  cx<R>* e = reinterpret_cast<cx<R>*>(cx_ws);       // batch x n
+  cx<R>* phi = e + (long long)batch * n;            // batch x n
+  cx<R>* P = phi + (long long)batch * n;            // batch x n
+  cx<R>* Vh = P + (long long)batch * n;             // batch x n x n
+  R* d = reinterpret_cast<R*>(re_ws);               // batch x n
+  R* eabs = d + (long long)batch * n;               // batch x n
+  R* lam = eabs + (long long)batch * n;             // batch x n
+  double* Kp = reinterpret_cast<double*>(lam + (long long)batch * n + 1);
+  Kp = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(Kp) + 15) & ~uintptr_t(15));
+  cudaError_t ce = cudaMemsetAsync(Vh, 0, sizeof(cx<R>) * (size_t)batch * n * n, st);
+  if (ce != cudaSuccess) return ce;
+  if (smem_cluster_size<R>(n) > 0) {
+    ce = tridiag_smem<R>(st, H, sH, n, d, e, n, Vh, (long long)n * n, batch);
+  } else {
+    const int cs = cluster_size_for(n);
+    ProfScope ps(st, K_TRIDIAG, 1, 16.0 / 3.0 * (double)n * n * n * batch);
+    ce = launch_cluster(tridiag_kernel<R>, cs, batch, 2 * sizeof(cx<R>) * (size_t)n, st, H, sH, n, d, e, n, P, Kp,
+                        Vh, (long long)n * n);
+  }
+  if (ce != cudaSuccess) return ce;
+  {
+    ProfScope ps(st, K_ELEMWISE);
+    tridiag_phases_kernel<R><<<batch, 256, 0, st>>>(e, n, n, eabs, phi);
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  const int total = batch * n;
+  {
+    ProfScope ps(st, K_BISECT);
+    bisect_kernel<R><<<(total * 32 + 255) / 256, 256, 0, st>>>(d, eabs, n, n, n, lam, n, total);
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  {
+    ProfScope ps(st, K_ELEMWISE);
+    entropy_kernel<R><<<batch, 256, 0, st>>>(lam, n, n, S, sS);
+  }
+  return cudaGetLastError();
+}
+
 #define NNE_INST_LINALG(R)                                                                                       \
   template cudaError_t eigh_top<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, void*, void*, \
-                                   void*, int, int*);
+                                   void*, int, int*);                                                       \
+  template cudaError_t gram_entropy<R>(cudaStream_t, cx<R>*, long long, int, void*, void*, int, double*, long long);
 NNE_INST_LINALG(float)
 NNE_INST_LINALG(double)
 

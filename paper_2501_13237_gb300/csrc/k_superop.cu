@@ -138,6 +138,54 @@ __global__ void __launch_bounds__(256) gate_superop_kernel(int n_gates, const do
   G[2 * o + 1] = acc.im;
 }
 
+// Gate-dependent Pauli noise (cat-qubit, App. C.2.2; matchgate depolarizing,
+// App. C.3.1): G[z][g] = S_P (U_g (x) conj U_g) with
+// S_P = sum_ab p_ab (s_a (x) s_b) (x) conj(s_a (x) s_b) and
+// p_ab = c0[g][ab] + lambda_z c1[g][ab] (ab = 4a + b, a on the left qubit).
+// One block per (gate, level); thread (row, col) forms one entry of each factor.
+__global__ void __launch_bounds__(256) pauli_superop_kernel(int n_gates, const double* U, const double* pr,
+                                                            const double* lam, double* G) {
+  __shared__ cx<double> u[16];
+  __shared__ cx<double> sig[4][4];
+  __shared__ double p[16];
+  __shared__ cx<double> SU[256], SP[256];
+  const int g = blockIdx.x, z = blockIdx.y, tid = threadIdx.x;
+  if (tid < 16) {
+    u[tid] = mk<double>(U[32 * g + 2 * tid], U[32 * g + 2 * tid + 1]);
+    p[tid] = pr[32LL * g + tid] + lam[z] * pr[32LL * g + 16 + tid];
+  }
+  if (tid < 4) pauli(tid, sig[tid]);
+  __syncthreads();
+  const int row = tid >> 4, col = tid & 15;
+  const int s1 = row >> 2, s2 = row & 3, t1 = col >> 2, t2 = col & 3;
+  const int i1 = s1 >> 1, j1 = s1 & 1, i2 = s2 >> 1, j2 = s2 & 1;
+  const int k1 = t1 >> 1, l1 = t1 & 1, k2 = t2 >> 1, l2 = t2 & 1;
+  SU[tid] = u[4 * (2 * i1 + i2) + (2 * k1 + k2)] * conj(u[4 * (2 * j1 + j2) + (2 * l1 + l2)]);
+  cx<double> acc = mk<double>(0, 0);
+  for (int a = 0; a < 4; ++a) {
+    const cx<double> fa = sig[a][2 * i1 + k1] * conj(sig[a][2 * j1 + l1]);
+    for (int b = 0; b < 4; ++b) {
+      const cx<double> fb = sig[b][2 * i2 + k2] * conj(sig[b][2 * j2 + l2]);
+      acc = acc + p[4 * a + b] * (fa * fb);
+    }
+  }
+  SP[tid] = acc;
+  __syncthreads();
+  acc = mk<double>(0, 0);
+  for (int q = 0; q < 16; ++q) fma_(acc, SP[16 * row + q], SU[16 * q + col]);
+  const long long o = ((long long)z * n_gates + g) * 256 + tid;
+  G[2 * o] = acc.re;
+  G[2 * o + 1] = acc.im;
+}
+
+cudaError_t build_pauli_superops(cudaStream_t st, int n_gates, const double* d_U, const double* d_pr, int n_inst,
+                                 const double* d_lam, double* d_G) {
+  if (n_gates <= 0 || n_inst <= 0) return cudaSuccess;
+  ProfScope ps(st, K_SUPEROP_BUILD, 1);
+  pauli_superop_kernel<<<dim3(n_gates, n_inst), 256, 0, st>>>(n_gates, d_U, d_pr, d_lam, d_G);
+  return cudaGetLastError();
+}
+
 cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int n_inst, const double* d_rates,
                            double* d_G, double* d_Snoise) {
   ProfScope ps(st, K_SUPEROP_BUILD, 2);

@@ -64,6 +64,14 @@ template <typename R>
 cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R>* U, long long sU, void* cx_ws,
                      void* re_ws, void* u8_ws, int batch, int* err);
 
+// Entropy -sum p ln p of the normalised eigenvalues p of each Hermitian
+// positive semi-definite H[z] (n x n, overwritten), written to S[z * sS]:
+// with H the Gram matrix of a canonical-form centre tensor it is the MPO
+// entanglement entropy of that bond.  Workspace as eigh_workspace(n, n).
+template <typename R>
+cudaError_t gram_entropy(cudaStream_t st, cx<R>* H, long long sH, int n, void* cx_ws, void* re_ws, int batch,
+                         double* S, long long sS);
+
 template <typename R>
 int smem_cluster_size(int n);
 template <typename R>
@@ -111,6 +119,9 @@ cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* 
 // ---- k_superop.cu
 cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int n_inst, const double* d_rates,
                            double* d_G, double* d_Snoise /* n_inst x 256 complex128 scratch */);
+// Gate-dependent Pauli channels: d_pr n_gates x 2 x 16 (c0, c1), d_lam n_inst.
+cudaError_t build_pauli_superops(cudaStream_t st, int n_gates, const double* d_U, const double* d_pr, int n_inst,
+                                 const double* d_lam, double* d_G);
 
 // ---- k_fit.cu
 cudaError_t extrapolate_fit(cudaStream_t st, int n_lambda, const double* d_lam, const double* d_vals,

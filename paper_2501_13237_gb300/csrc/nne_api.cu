@@ -3,6 +3,7 @@
 // centre moves), the expectation sweep and the extrapolation fit.  Every
 // arithmetic step runs in the kernels of k_*.cu; this file only sizes
 // buffers, tracks bond dimensions and enqueues launches.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -520,6 +521,28 @@ nne_status compress(nne_state* s, int chi_new) {
   return NNE_OK;
 }
 
+// MPO entanglement entropy of every bond (App. A.1): centre to site 0, then
+// for k = 0 .. n-2 the Gram matrix M_k^H M_k of the centre tensor (its
+// eigenvalues are the squared Schmidt values of bond k | k+1) and a QR step
+// that moves the centre on.  S[z * (n - 1) + k] on the device.
+template <typename R>
+nne_status entropy_sweep(nne_state* s, double* S) {
+  const BatchView b{s->ctx->stream, 0, s->n_inst};
+  const std::vector<BatchView> views{b};
+  cudaStream_t st = b.st;
+  TRY(move_centre<R>(s, views, 0));
+  for (int k = 0; k + 1 < s->n; ++k) {
+    const int dl = s->dims[k], dr = s->dims[k + 1];
+    cx<R>* M = spb<R>(s, b, k);
+    cx<R>* Hm = wsb<R>(s->H, s->sH, b);
+    CTRY(cgemm<R>(st, OP_C, OP_N, dr, dr, 4 * dl, mk<R>(1, 0), M, s->sstride[k], dr, M, s->sstride[k], dr,
+                  mk<R>(0, 0), Hm, s->sH, dr, b.nb));
+    CTRY(gram_entropy<R>(st, Hm, s->sH, dr, eigcx<R>(s, b), eigre<R>(s, b), b.nb, S + k, s->n - 1));
+    TRY(move_centre<R>(s, views, k + 1));
+  }
+  return NNE_OK;
+}
+
 nne_status read_err(nne_state* s) {
   int h = 0, t = 0;
   cudaError_t e = cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->ctx->stream);
@@ -617,6 +640,49 @@ nne_status nne_build_superops(nne_ctx* ctx, int n_gates, const double* U, int n_
   cudaFreeAsync(dU, ctx->stream);
   cudaFreeAsync(dR, ctx->stream);
   cudaFreeAsync(dS, ctx->stream);
+  return rc;
+}
+
+nne_status nne_build_pauli_superops(nne_ctx* ctx, int n_gates, const double* U, const double* pauli_rates,
+                                    int n_inst, const double* lambdas, void* G_out) {
+  if (!ctx || n_gates < 0 || n_inst < 1 || !lambdas || (n_gates > 0 && (!U || !pauli_rates || !G_out)))
+    return set_error(NNE_ERR_ARG, "nne_build_pauli_superops: bad arguments");
+  if (n_gates == 0) return NNE_OK;
+  DeviceGuard g(ctx->device);
+  const bool u_dev = is_device_ptr(U), p_dev = is_device_ptr(pauli_rates), l_dev = is_device_ptr(lambdas);
+  if (!p_dev && !l_dev)
+    for (int i = 0; i < n_inst; ++i)
+      for (int k = 0; k < n_gates; ++k) {
+        double tot = 0;
+        for (int ab = 0; ab < 16; ++ab) {
+          const double p = pauli_rates[32LL * k + ab] + lambdas[i] * pauli_rates[32LL * k + 16 + ab];
+          if (!(p >= -1e-12 && p <= 1.0 + 1e-12))
+            return set_error(NNE_ERR_ARG, "Pauli probability %d of gate %d at level %d out of [0,1]: %g", ab, k, i, p);
+          tot += p;
+        }
+        if (!(std::fabs(tot - 1.0) <= 1e-12))
+          return set_error(NNE_ERR_ARG, "Pauli probabilities of gate %d at level %d sum to %.17g", k, i, tot);
+      }
+  if (u_dev && p_dev && l_dev) {
+    NNE_CUDA_TRY(build_pauli_superops(ctx->stream, n_gates, U, pauli_rates, n_inst, lambdas, (double*)G_out));
+    return NNE_OK;
+  }
+  double *dU = nullptr, *dP = nullptr, *dL = nullptr;
+  const size_t bu = sizeof(double) * 32 * (size_t)n_gates, bp = sizeof(double) * 32 * (size_t)n_gates,
+               bl = sizeof(double) * n_inst;
+  NNE_CUDA_TRY(cudaMallocAsync(&dU, bu, ctx->stream));
+  NNE_CUDA_TRY(cudaMallocAsync(&dP, bp, ctx->stream));
+  NNE_CUDA_TRY(cudaMallocAsync(&dL, bl, ctx->stream));
+  nne_status rc = NNE_OK;
+  cudaError_t e = cudaMemcpyAsync(dU, U, bu, cudaMemcpyDefault, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dP, pauli_rates, bp, cudaMemcpyDefault, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dL, lambdas, bl, cudaMemcpyDefault, ctx->stream);
+  if (e == cudaSuccess) e = build_pauli_superops(ctx->stream, n_gates, dU, dP, n_inst, dL, (double*)G_out);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) rc = set_cuda_error(e, "build_pauli_superops", __FILE__, __LINE__);
+  cudaFreeAsync(dU, ctx->stream);
+  cudaFreeAsync(dP, ctx->stream);
+  cudaFreeAsync(dL, ctx->stream);
   return rc;
 }
 
@@ -847,6 +913,22 @@ nne_status nne_truncate(nne_state* st, int chi_new, double* log_fid_out) {
   if (log_fid_out)
     for (int i = 0; i < st->n_inst; ++i) log_fid_out[i] = after[i] - before[i];
   return NNE_OK;
+}
+
+nne_status nne_entropy(nne_state* st, double* S_out) {
+  if (!st || !S_out) return set_error(NNE_ERR_ARG, "nne_entropy: bad arguments");
+  if (st->n < 2) return NNE_OK;
+  DeviceGuard dg(st->ctx->device);
+  const size_t bytes = sizeof(double) * (size_t)st->n_inst * (st->n - 1);
+  double* dS = nullptr;
+  NNE_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&dS), bytes, st->ctx->stream));
+  nne_status rc = st->dtype == NNE_C64 ? entropy_sweep<float>(st, dS) : entropy_sweep<double>(st, dS);
+  cudaError_t ce = cudaSuccess;
+  if (rc == NNE_OK) ce = cudaMemcpyAsync(S_out, dS, bytes, cudaMemcpyDeviceToHost, st->ctx->stream);
+  cudaFreeAsync(dS, st->ctx->stream);
+  if (rc != NNE_OK) return rc;
+  if (ce != cudaSuccess) return set_cuda_error(ce, "cudaMemcpyAsync", __FILE__, __LINE__);
+  return read_err(st);
 }
 
 nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* re_out, double* im_out,

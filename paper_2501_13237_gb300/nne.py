@@ -31,7 +31,7 @@ SYMBOLS = (
     "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
     "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
-    "nne_extrapolate_ladder",
+    "nne_extrapolate_ladder", "nne_entropy", "nne_build_pauli_superops",
 )
 SERVER_DRYRUN = 1
 
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
         "nne_apply_layer": (i32, [vp, i32, vp, vp, i32]),
         "nne_truncate": (i32, [vp, i32, vp]),
         "nne_expect": (i32, [vp, i32, vp, vp, vp, vp]),
+        "nne_entropy": (i32, [vp, vp]),
+        "nne_build_pauli_superops": (i32, [vp, i32, vp, vp, i32, vp, vp]),
         "nne_extrapolate": (i32, [vp, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp]),
         "nne_sync": (i32, [vp]),
         "nne_state_info": (i32, [vp, vp, vp, vp, vp]),
@@ -173,6 +175,21 @@ class Context:
         G = out if out is not None else torch.empty((ni, g, 16, 16), dtype=torch.complex128,
                                                     device=f"cuda:{self.device}")
         _check(load().nne_build_superops(self.h, g, pu[0], ni, pr[0], C.c_void_p(_dptr(G))))
+        return G
+
+    def build_pauli_superops(self, U, c0, c1, lambdas, out=None):
+        """a1 for gate-dependent Pauli noise: U (g,4,4) complex128, c0 / c1 (g,16)
+        probabilities at lambda = 0 and their slopes, lambdas (n_inst,) -> device
+        tensor (n_inst, g, 16, 16) complex128."""
+        import torch
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        pr = np.ascontiguousarray(np.stack([np.asarray(c0, float), np.asarray(c1, float)], axis=1))
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        g, ni = U.shape[0], lam.size
+        G = out if out is not None else torch.empty((ni, g, 16, 16), dtype=torch.complex128,
+                                                    device=f"cuda:{self.device}")
+        _check(load().nne_build_pauli_superops(self.h, g, _hptr(U), _hptr(pr), ni, _hptr(lam),
+                                               C.c_void_p(_dptr(G))))
         return G
 
     def extrapolate(self, lambdas, values, log_fid=None, method=FIT_EXP_LOGLIN, degree=2, lambda_star=1.0,
@@ -297,6 +314,12 @@ class State:
         lf = np.zeros(self.n_inst)
         _check(load().nne_expect(self.h, no, _hptr(p), _hptr(re), _hptr(im), _hptr(lf)))
         return re + 1j * im, lf
+
+    def entropy(self) -> np.ndarray:
+        """MPO entanglement entropy per bond, (n_inst, n - 1); S_max is the row maximum."""
+        out = np.zeros((self.n_inst, max(self.n - 1, 0)))
+        _check(load().nne_entropy(self.h, _hptr(out)))
+        return out
 
     def sync(self):
         _check(load().nne_sync(self.h))

@@ -28,6 +28,21 @@ def layer_plan(circuit) -> List[Tuple[List[int], np.ndarray, int]]:
     return plan
 
 
+def build_pauli_layers(ctx: nne.Context, pc, lambdas):
+    """Device superoperators for every layer of a Pauli-noise circuit (gate-
+    dependent channels, e.g. cat-qubit or matchgate noise), one instance per
+    level in lambdas, in the snake schedule's application order."""
+    out = []
+    for t, (qs, us) in enumerate(zip(pc.layers, pc.unitaries)):
+        if len(qs) == 0:
+            continue
+        order = slice(None) if t % 2 == 0 else slice(None, None, -1)
+        G = ctx.build_pauli_superops(np.asarray(us)[order], np.asarray(pc.c0[t])[order],
+                                     np.asarray(pc.c1[t])[order], lambdas)
+        out.append((list(qs)[order], G, +1 if t % 2 == 0 else -1))
+    return out
+
+
 def build_layer_superops(ctx: nne.Context, circuit, rates: np.ndarray):
     """Device superoperators for every layer (a1), in application order."""
     return [(qs, ctx.build_superops(us, rates), d) for qs, us, d in layer_plan(circuit)]
@@ -42,7 +57,8 @@ def emulate(ctx: nne.Context, circuit, rates: np.ndarray, chi: int, paulis: np.n
             trunc: int = nne.TRUNC_EXACT, bits=None, layers=None):
     """Run one circuit at all noise levels (one instance per row of rates).
     Returns (state, <P> (n_inst, n_obs) complex, log F (n_inst))."""
-    st = nne.State(ctx, circuit.n, chi, rates.shape[0], dtype, trunc, bits)
+    n_inst = rates.shape[0] if rates is not None else layers[0][1].shape[0]
+    st = nne.State(ctx, circuit.n, chi, n_inst, dtype, trunc, bits)
     evolve(st, layers if layers is not None else build_layer_superops(ctx, circuit, rates))
     vals, lf = st.expect(paulis)
     return st, vals, lf
@@ -66,11 +82,12 @@ def job_for(w, chi=None, dtype: int = nne.C64, trunc: int = nne.TRUNC_EXACT, ske
 
 
 def emulate_ladder(ctx: nne.Context, circuit, rates: np.ndarray, chis, paulis: np.ndarray, dtype: int = nne.C64,
-                   trunc: int = nne.TRUNC_EXACT, bits=None):
+                   trunc: int = nne.TRUNC_EXACT, bits=None, layers=None):
     """The same circuit at every noise level for each bond dimension of a ladder
     D_1 < ... < D_k (one state per rung).  Returns values (k, n_inst, n_obs)
-    (real parts) and log F (k, n_inst) for nne_extrapolate_ladder."""
-    layers = build_layer_superops(ctx, circuit, rates)
+    (real parts) and log F (k, n_inst) for nne_extrapolate_ladder.  `layers`
+    (prebuilt superoperators) replaces `rates` when given."""
+    layers = build_layer_superops(ctx, circuit, rates) if layers is None else layers
     vals, lfs = [], []
     for chi in chis:
         st, v, lf = emulate(ctx, circuit, rates, int(chi), paulis, dtype, trunc, bits, layers)
@@ -88,11 +105,16 @@ def nzne(ctx: nne.Context, circuit, noise, lambdas, chis, paulis: np.ndarray, la
     (A), then extrapolation in the noise strength to lambda* (B).  The
     lambda = 0 emulation at the largest chi is the sign reference of
     criterion 3 and does not enter the fit.  `noise` is a workloads.NoiseModel
-    (strengths scaled by lambda)."""
+    (strengths scaled by lambda), or None for a circuit that carries its own
+    gate-dependent Pauli channels (c0 + lambda c1 per gate)."""
     lam = np.asarray(lambdas, np.float64)
     levels = ([0.0] if with_zero else []) + list(lam)
-    rates = np.stack([noise.rates(l) for l in levels])
-    vals, lfs = emulate_ladder(ctx, circuit, rates, chis, paulis, dtype, bits=bits)
+    if noise is None:
+        layers = build_pauli_layers(ctx, circuit, np.asarray(levels, np.float64))
+        vals, lfs = emulate_ladder(ctx, circuit, None, chis, paulis, dtype, bits=bits, layers=layers)
+    else:
+        rates = np.stack([noise.rates(l) for l in levels])
+        vals, lfs = emulate_ladder(ctx, circuit, rates, chis, paulis, dtype, bits=bits)
     y_zero = None
     if with_zero:
         y_zero = vals[-1, 0].copy()
