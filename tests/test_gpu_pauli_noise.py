@@ -80,8 +80,9 @@ def test_cat_circuit_vs_oracle(ctx, dtype, tol):
     # cuts; this seed and chi keep every cut gapped (s_5 / s_4 <= 0.68).
     # complex64: the rank of this state at most cuts is below chi, so the kept
     # set holds null directions; a float32 Gram eigensolve leaves them with
-    # noise of size sqrt(eps_32) s_1 ~ 3.5e-4 s_1 instead of zeros (measured
-    # error 3.2e-3 at lambda = 0.02).  Full-rank cuts (Haar and XY-model
+    # noise of size eps_32 s_1^2 / s_r (up to sqrt(eps_32) s_1 ~ 3.5e-4 s_1,
+    # s_r the smallest non-zero kept value) instead of zeros (measured error
+    # 3.2e-3 at lambda = 0.02).  Full-rank cuts (Haar and XY-model
     # circuits) meet 1e-4; the complex128 path meets 1e-8 here.
     pc = wl.cat_circuit(10, 24, 7)
     assert _vmpo_parity(ctx, pc, (0.0, 0.005, 0.02), 4, dtype, tol)
