@@ -30,6 +30,9 @@ cpu_baseline / --impl reference: the CPU oracle (NumPy, float64) timed on a
 serving    an open-loop Poisson request stream through nne_submit / nne_poll
            (whole jobs, 4 worker streams; sizes reduced, see serving_run):
            p50 / p99 latency, requests/s and gate steps/s.
+batch      the 64-circuit batch workload (n 16-64, depth 10-40, chi 32-128,
+           5 levels, complex64) submitted at once to the same server: gate
+           steps/s and circuits/s over the whole batch (see batch_run).
 
 Multi-GPU: replicas only (each rank runs its own instance of the job with its
 own circuit seed, no data-path collective; scaling "weak").
@@ -157,6 +160,8 @@ def main():
     ap.add_argument("--serving", type=int, default=40,
                     help="requests of the open-loop serving sample added to the line (0: none)")
     ap.add_argument("--serving-rate", type=float, default=20.0, help="offered requests per second")
+    ap.add_argument("--batch", type=int, default=64,
+                    help="circuits of the 64-circuit batch workload added to the line (0: none)")
     ap.add_argument("--subbatches", type=int, default=None,
                     help="concurrent sub-batches per state (NNE_OPT_SUBBATCHES; library default when omitted)")
     args = ap.parse_args()
@@ -299,6 +304,9 @@ def main():
     serving = None
     if rank == 0 and args.serving > 0:
         serving = serving_run(args.serving, args.serving_rate, 0, 4, local)
+    batch = None
+    if rank == 0 and args.batch > 0:
+        batch = batch_run(args.batch, 4, local)
     if rank == 0:
         line = {"metric": "2q gate+truncation steps/s at chi=512", "value": value, "unit": "gate_steps/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -312,7 +320,7 @@ def main():
                 "e2e": {"value": e2e, "unit": "gate_steps/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
-                "kernel_classes_ms": prof_summary, "serving": serving}
+                "kernel_classes_ms": prof_summary, "serving": serving, "batch": batch}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -385,6 +393,28 @@ def serving_run(n_requests: int, rate_per_s: float, seed: int, workers: int, dev
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "requests_per_s": n_requests / span, "gate_steps_per_s": steps / span,
             "sizes": "n 8-32, depth 5-20, chi 16-128, 4-8 levels, c64 exact truncation"}
+
+
+def batch_run(n_circuits: int, workers: int, device: int = 0):
+    """The 64-circuit batch workload (n ~ U[16,64], depth ~ U[10,40], chi in
+    {32, 64, 128}, 5 levels of depolarizing + dephasing, all <Z_i>, exponential
+    fit; complex64, exact truncation) submitted at once to a server with
+    `workers` streams: wall time from the first submit to the last completion."""
+    import workloads as wl
+    from paper_2501_13237_gb300 import nne, runner
+    ws = wl.batch64(0, n_circuits)
+    jobs = [runner.job_for(w, dtype=nne.C64) for w in ws]
+    srv = nne.Server(device, hbm_budget_bytes=150 << 30, workers=workers)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(j) for j in jobs]
+    res = [srv.poll(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    srv.close()
+    steps = sum(r["gate_steps"] for r in res)
+    return {"circuits": n_circuits, "workers": workers, "failed": sum(r["status"] != 0 for r in res),
+            "wall_s": wall, "gate_steps": int(steps), "gate_steps_per_s": steps / wall,
+            "circuits_per_s": n_circuits / wall,
+            "sizes": "n 16-64, depth 10-40, chi 32/64/128, 5 levels, c64 exact truncation"}
 
 
 if __name__ == "__main__":
