@@ -23,8 +23,9 @@ e2e        the same metric with the step's inputs copied from pinned host
            memory and <P>, log F and the fit read back every step.
 roofline   the dominant kernel class from live CUDA-event timing of one more
            step run with per-launch event pairs (nne_prof_collect; the
-           headline steps are timed without them), achieved = algorithmic
-           flops per launch / average launch time.
+           headline steps are timed without them) and its layers on one
+           stream (NNE_OPT_SERIAL_LAYERS), so that each launch is timed alone;
+           achieved = algorithmic flops per launch / average launch time.
 cpu_baseline / --impl reference: the CPU oracle (NumPy, float64) timed on a
            bounded sample: full-size gate steps at chi = 512 on the host cores.
 serving    an open-loop Poisson request stream through nne_submit / nne_poll
@@ -278,8 +279,11 @@ def main():
     clk = clocks.stop()
     ms_e2e, _, _, units_e2e = timed(True, 1)
     # per-kernel-class breakdown from a separate profiled step (event pairs around
-    # every launch add host work, so the headline is timed without them)
+    # every launch add host work, so the headline is timed without them); its
+    # layers run on one stream, so each launch's events time that kernel alone
+    nne.set_option(nne.OPT_SERIAL_LAYERS, 1)
     ms_prof, _, prof, _ = timed(False, 1, prof=True)
+    nne.set_option(nne.OPT_SERIAL_LAYERS, 0)
 
     value = units / (ms / 1e3)
     e2e = units_e2e / (ms_e2e / 1e3)

@@ -263,9 +263,14 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
  * back to the context stream), so that the latency-bound kernels of one
  * overlap the GEMMs of another.  States whose largest bond is below 256 use
  * one stream (their kernels are small and splitting multiplies launches).
- * Results do not depend on it beyond the rounding of GEMM split choices. */
+ * Results do not depend on it beyond the rounding of GEMM split choices.
+ * NNE_OPT_SERIAL_LAYERS (default 0): when 1, nne_apply_layer runs all of a
+ * state's instances as one batch on the context stream, whatever the state's
+ * sub-batch count -- for per-launch timing of the kernels alone.
+ * Options are process-wide; set them while no other thread calls the library. */
 #define NNE_OPT_TENSOR_CORES 0
 #define NNE_OPT_SUBBATCHES 1
+#define NNE_OPT_SERIAL_LAYERS 2
 void nne_set_option(int option, int value);
 
 /* Wait for the state's enqueued work; returns the first device-side error. */

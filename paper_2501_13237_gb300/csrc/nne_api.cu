@@ -213,6 +213,9 @@ namespace {
 
 // Sub-batches a new state splits its instances into (nne_set_option).
 int g_substreams = 4;
+// When set, nne_apply_layer runs every state's instances as one batch on the
+// context stream (nne_set_option NNE_OPT_SERIAL_LAYERS).
+int g_serial_layers = 0;
 
 void destroy_streams(nne_state* s) {
   for (cudaStream_t q : s->sub_st) cudaStreamDestroy(q);
@@ -878,21 +881,22 @@ nne_status nne_apply_layer(nne_state* st, int n_gates, const int* left_qubit, co
   const long long sG = (long long)n_gates * 256;   // complex elements between instances
   // the instances split into nsub views, each on its own stream, forked from and joined back
   // to the context stream; gate by gate the host enqueues every view's work in turn
+  const int nv = g_serial_layers ? 1 : st->nsub;
   std::vector<BatchView> views;
-  for (int v = 0; v < st->nsub; ++v) {
-    const int i0 = (int)((long long)st->n_inst * v / st->nsub), i1 = (int)((long long)st->n_inst * (v + 1) / st->nsub);
-    views.push_back(BatchView{st->nsub > 1 ? st->sub_st[v] : st->ctx->stream, i0, i1 - i0});
+  for (int v = 0; v < nv; ++v) {
+    const int i0 = (int)((long long)st->n_inst * v / nv), i1 = (int)((long long)st->n_inst * (v + 1) / nv);
+    views.push_back(BatchView{nv > 1 ? st->sub_st[v] : st->ctx->stream, i0, i1 - i0});
   }
-  if (st->nsub > 1) {
+  if (nv > 1) {
     NNE_CUDA_TRY(cudaEventRecord(st->ev_fork, st->ctx->stream));
-    for (int v = 0; v < st->nsub; ++v) NNE_CUDA_TRY(cudaStreamWaitEvent(st->sub_st[v], st->ev_fork, 0));
+    for (int v = 0; v < nv; ++v) NNE_CUDA_TRY(cudaStreamWaitEvent(st->sub_st[v], st->ev_fork, 0));
   }
   nne_status rc = NNE_OK;
   for (int g = 0; g < n_gates && rc == NNE_OK; ++g)
     rc = st->dtype == NNE_C64 ? gate_step<float>(st, views, left_qubit[g], Gd + 2LL * 256 * g, sG, direction)
                               : gate_step<double>(st, views, left_qubit[g], Gd + 2LL * 256 * g, sG, direction);
-  if (st->nsub > 1)
-    for (int v = 0; v < st->nsub; ++v) {
+  if (nv > 1)
+    for (int v = 0; v < nv; ++v) {
       cudaEventRecord(st->ev_join[v], st->sub_st[v]);
       cudaStreamWaitEvent(st->ctx->stream, st->ev_join[v], 0);
     }
@@ -1094,6 +1098,7 @@ nne_status nne_reset_state(nne_state* st, const uint8_t* init_bits) {
 void nne_set_option(int option, int value) {
   if (option == NNE_OPT_TENSOR_CORES) set_tensor_cores(value);
   if (option == NNE_OPT_SUBBATCHES) g_substreams = value < 1 ? 1 : (value > 8 ? 8 : value);
+  if (option == NNE_OPT_SERIAL_LAYERS) g_serial_layers = value ? 1 : 0;
 }
 
 nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, const float* alpha, const void* A,

@@ -268,6 +268,7 @@ def set_option(option: int, value: int):
 
 OPT_TENSOR_CORES = 0
 OPT_SUBBATCHES = 1
+OPT_SERIAL_LAYERS = 2
 
 
 class State:

@@ -201,3 +201,27 @@ def test_fit_kernel_vs_oracle(ctx, method):
     assert (st == rst).all()
     tol = 1e-10 if method != 2 else 1e-7
     assert np.abs(est - ref).max() < tol * max(1.0, np.abs(ref).max()), np.abs(est - ref).max()
+
+
+def test_serial_layers_option_matches_sub_batches(ctx):
+    """NNE_OPT_SERIAL_LAYERS runs a sub-batched state's layers on one stream:
+    same results up to the rounding of GEMM split choices."""
+    from paper_2501_13237_gb300 import nne, runner
+    n, chi = 10, 256
+    c = wl.brickwork_circuit(n, 7, 31)
+    rates = np.stack([wl.NoiseModel(depol2=0.01, dephase=0.005).rates(l) for l in (1, 2, 3, 4)])
+    paulis = wl.pauli_codes(wl.obs_z(n) + wl.obs_xx(n), n)
+    layers = runner.build_layer_superops(ctx, c, rates)
+    out = []
+    for serial in (0, 1):
+        nne.set_option(nne.OPT_SERIAL_LAYERS, serial)
+        try:
+            st, vals, lf = runner.emulate(ctx, c, rates, chi, paulis, nne.C64, layers=layers)
+            st.close()
+        finally:
+            nne.set_option(nne.OPT_SERIAL_LAYERS, 0)
+        out.append((vals, lf))
+    # complex64 tolerance: split-K choices depend on the batch size (measured 1.7e-5)
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-4
+    assert np.abs(out[0][1] - out[1][1]).max() < 1e-4
+    assert (out[0][1] < -1e-4).all()          # truncation happens (bond 256 < 4^5)
