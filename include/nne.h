@@ -340,7 +340,7 @@ typedef struct {
   const double* U;          /* sum(layer_gates) x 4 x 4 complex128 (re, im interleaved), row-major */
   int n_lambda;
   const double* lambdas;    /* n_lambda noise levels */
-  const double* rates;      /* n_lambda x 4 channel strengths, as nne_build_superops */
+  const double* rates;      /* n_lambda x 4 channel strengths, as nne_build_superops (NULL with pauli_rates) */
   int chi;
   int dtype;                /* nne_dtype */
   int trunc;                /* nne_trunc */
@@ -352,6 +352,10 @@ typedef struct {
   int fit_method;           /* nne_fit */
   int fit_degree;           /* NNE_FIT_POLY only */
   double lambda_star;
+  const double* pauli_rates; /* NULL, or sum(layer_gates) x 2 x 16: gate-dependent Pauli channels as
+                                nne_build_pauli_superops (c0, c1 per gate, in gate order); when set,
+                                rates is ignored and level i applies p = c0 + lambdas[i] c1, each
+                                in [0, 1] and summing to 1 per gate (checked at submit) */
 } nne_job;
 
 typedef struct {

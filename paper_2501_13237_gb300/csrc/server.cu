@@ -10,6 +10,7 @@
 // nne_build_superops, nne_apply_layer, nne_expect, nne_extrapolate); this
 // file holds no arithmetic of the method.
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -35,7 +36,7 @@ struct JobCopy {
   double lambda_star = 1.0;
   bool has_bits = false;
   std::vector<int> layer_gates, layer_dir, left_qubit;
-  std::vector<double> U, lambdas, rates;
+  std::vector<double> U, lambdas, rates, pauli;   // pauli: 32 per gate (c0, c1), empty for rate channels
   std::vector<char> sketch;
   std::vector<uint8_t> bits, paulis;
   size_t bytes = 0;
@@ -100,14 +101,22 @@ nne_status run_job(nne_ctx* ctx, cudaStream_t st, const JobCopy& j, ResultRec& r
       return rc;
     }
   }
+  // rate channels: dRates = n_lambda x 4; Pauli channels: 32 per gate (c0, c1), then the n_lambda levels
+  const bool pauli = !j.pauli.empty();
+  const size_t n_rates = pauli ? (size_t)32 * j.gates + j.n_lambda : (size_t)4 * j.n_lambda;
   cudaError_t e = cudaMallocAsync((void**)&dU, sizeof(double) * 32 * (size_t)std::max<long long>(j.gates, 1), st);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dRates, sizeof(double) * 4 * j.n_lambda, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&dRates, sizeof(double) * n_rates, st);
   if (e == cudaSuccess)
     e = cudaMallocAsync((void**)&dG, sizeof(double) * 512 * (size_t)j.n_lambda * std::max(j.max_layer_gates, 1), st);
   if (e == cudaSuccess && j.gates > 0)
     e = cudaMemcpyAsync(dU, j.U.data(), sizeof(double) * 32 * j.gates, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && !pauli)
     e = cudaMemcpyAsync(dRates, j.rates.data(), sizeof(double) * 4 * j.n_lambda, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && pauli)
+    e = cudaMemcpyAsync(dRates, j.pauli.data(), sizeof(double) * 32 * j.gates, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && pauli)
+    e = cudaMemcpyAsync(dRates + 32 * j.gates, j.lambdas.data(), sizeof(double) * j.n_lambda, cudaMemcpyHostToDevice,
+                        st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host vectors are the job's own; keep them simple
   if (e != cudaSuccess) {
     cleanup();
@@ -117,7 +126,9 @@ nne_status run_job(nne_ctx* ctx, cudaStream_t st, const JobCopy& j, ResultRec& r
   for (int l = 0; l < j.n_layers && rc == NNE_OK; ++l) {
     const int g = j.layer_gates[l];
     if (g == 0) continue;
-    rc = nne_build_superops(ctx, g, dU + 32 * off, j.n_lambda, dRates, dG);
+    rc = pauli ? nne_build_pauli_superops(ctx, g, dU + 32 * off, dRates + 32 * off, j.n_lambda, dRates + 32 * j.gates,
+                                          dG)
+               : nne_build_superops(ctx, g, dU + 32 * off, j.n_lambda, dRates, dG);
     if (rc == NNE_OK) rc = nne_apply_layer(s, g, j.left_qubit.data() + off, dG, j.layer_dir[l]);
     off += g;
   }
@@ -205,7 +216,8 @@ void worker_main(nne_server* srv) {
 
 nne_status copy_job(const nne_job* j, JobCopy& c) {
   if (!j || j->n_qubits < 2 || j->n_layers < 0 || (j->n_layers > 0 && (!j->layer_gates || !j->layer_dir)) ||
-      j->n_lambda < 1 || j->n_lambda > 64 || !j->lambdas || !j->rates || j->chi < 1 || j->chi > 4096 ||
+      j->n_lambda < 1 || j->n_lambda > 64 || !j->lambdas || (!j->rates && !j->pauli_rates) || j->chi < 1 ||
+      j->chi > 4096 ||
       (j->dtype != NNE_C64 && j->dtype != NNE_C128) || (j->trunc != NNE_TRUNC_EXACT && j->trunc != NNE_TRUNC_RSVD) ||
       j->n_obs < 0 || (j->n_obs > 0 && !j->paulis) || j->fit_method < 0 || j->fit_method > 2 ||
       (j->fit_method == NNE_FIT_POLY && (j->fit_degree < 1 || j->fit_degree > 15)))
@@ -237,13 +249,30 @@ nne_status copy_job(const nne_job* j, JobCopy& c) {
       return nne::set_error(NNE_ERR_ARG, "nne_submit: gate %lld: left qubit %d out of range", g, c.left_qubit[g]);
   c.U.assign(j->U, j->U + 32 * gates);
   c.lambdas.assign(j->lambdas, j->lambdas + c.n_lambda);
-  c.rates.assign(j->rates, j->rates + 4 * c.n_lambda);
-  for (int i = 0; i < c.n_lambda; ++i)
-    for (int k = 0; k < 4; ++k) {
-      const double p = c.rates[4 * i + k];
-      if (!(p >= 0.0 && p <= (k == 0 ? 16.0 / 15.0 : 1.0)))
-        return nne::set_error(NNE_ERR_ARG, "nne_submit: rate %d of level %d out of range: %g", k, i, p);
-    }
+  if (j->pauli_rates) {
+    c.pauli.assign(j->pauli_rates, j->pauli_rates + 32 * gates);
+    for (long long g = 0; g < gates; ++g)
+      for (int i = 0; i < c.n_lambda; ++i) {
+        double tot = 0;
+        for (int ab = 0; ab < 16; ++ab) {
+          const double p = c.pauli[32 * g + ab] + c.lambdas[i] * c.pauli[32 * g + 16 + ab];
+          if (!(p >= -1e-12 && p <= 1.0 + 1e-12))
+            return nne::set_error(NNE_ERR_ARG, "nne_submit: gate %lld level %d: Pauli probability %g", g, i, p);
+          tot += p;
+        }
+        if (!(std::fabs(tot - 1.0) <= 1e-12))
+          return nne::set_error(NNE_ERR_ARG, "nne_submit: gate %lld level %d: Pauli probabilities sum to %.17g", g,
+                                i, tot);
+      }
+  } else {
+    c.rates.assign(j->rates, j->rates + 4 * c.n_lambda);
+    for (int i = 0; i < c.n_lambda; ++i)
+      for (int k = 0; k < 4; ++k) {
+        const double p = c.rates[4 * i + k];
+        if (!(p >= 0.0 && p <= (k == 0 ? 16.0 / 15.0 : 1.0)))
+          return nne::set_error(NNE_ERR_ARG, "nne_submit: rate %d of level %d out of range: %g", k, i, p);
+      }
+  }
   if (c.trunc == NNE_TRUNC_RSVD) {
     if (!j->sketch || j->sketch_rows < 1 || j->sketch_cols < 1 || j->power_iters < 0)
       return nne::set_error(NNE_ERR_ARG, "nne_submit: randomized truncation needs a sketch");
@@ -277,7 +306,8 @@ size_t nne_job_bytes(const nne_job* j) {
   const int sk_cols = j->trunc == NNE_TRUNC_RSVD ? j->sketch_cols : 0;
   size_t b = nne::state_bytes(j->n_qubits, j->chi, j->n_lambda, j->dtype, j->sketch_rows, sk_cols);
   // staged gates, rates and one layer of superoperators (run_job)
-  b += r256(sizeof(double) * 32 * (size_t)std::max<long long>(gates, 1)) + r256(sizeof(double) * 4 * j->n_lambda) +
+  const size_t n_rates = j->pauli_rates ? (size_t)32 * gates + j->n_lambda : (size_t)4 * j->n_lambda;
+  b += r256(sizeof(double) * 32 * (size_t)std::max<long long>(gates, 1)) + r256(sizeof(double) * n_rates) +
        r256(sizeof(double) * 512 * (size_t)j->n_lambda * std::max(maxg, 1));
   // superoperator-build scratch of the worker's context, expectation and fit temporaries
   const size_t no = (size_t)std::max(j->n_obs, 1);

@@ -43,7 +43,8 @@ class JobStruct(C.Structure):
                 ("lambdas", C.c_void_p), ("rates", C.c_void_p), ("chi", C.c_int), ("dtype", C.c_int),
                 ("trunc", C.c_int), ("sketch", C.c_void_p), ("sketch_rows", C.c_int), ("sketch_cols", C.c_int),
                 ("power_iters", C.c_int), ("init_bits", C.c_void_p), ("n_obs", C.c_int), ("paulis", C.c_void_p),
-                ("fit_method", C.c_int), ("fit_degree", C.c_int), ("lambda_star", C.c_double)]
+                ("fit_method", C.c_int), ("fit_degree", C.c_int), ("lambda_star", C.c_double),
+                ("pauli_rates", C.c_void_p)]
 
 
 class ResultStruct(C.Structure):
@@ -378,11 +379,14 @@ class Job:
     """Host arrays of one nne_job, kept alive while the struct points at them.
 
     layers: sequence of (left_qubits, U (g,4,4) complex128, direction) in
-    application order; rates (n_lambda, 4) channel strengths per level."""
+    application order; rates (n_lambda, 4) channel strengths per level, or
+    pauli (gates, 2, 16): gate-dependent Pauli channels (c0, c1 per gate, in
+    the same order), with rates None."""
 
     def __init__(self, n: int, layers, lambdas, rates, chi: int, paulis, dtype: int = C64,
                  trunc: int = TRUNC_EXACT, sketch: Optional[np.ndarray] = None, power_iters: int = 1,
-                 bits=None, fit_method: int = FIT_EXP_LOGLIN, fit_degree: int = 2, lambda_star: float = 1.0):
+                 bits=None, fit_method: int = FIT_EXP_LOGLIN, fit_degree: int = 2, lambda_star: float = 1.0,
+                 pauli: Optional[np.ndarray] = None):
         self.n, self.chi = n, chi
         self.layer_gates = np.array([len(qs) for qs, _, _ in layers], dtype=np.int32)
         self.layer_dir = np.array([d for _, _, d in layers], dtype=np.int32)
@@ -392,7 +396,8 @@ class Job:
                                                       for _, us, _ in layers]) if layers
                                       else np.zeros((0, 4, 4), np.complex128))
         self.lambdas = np.ascontiguousarray(lambdas, dtype=np.float64)
-        self.rates = np.ascontiguousarray(rates, dtype=np.float64).reshape(-1, 4)
+        self.rates = None if rates is None else np.ascontiguousarray(rates, dtype=np.float64).reshape(-1, 4)
+        self.pauli = None if pauli is None else np.ascontiguousarray(pauli, dtype=np.float64).reshape(-1, 2, 16)
         self.paulis = np.ascontiguousarray(paulis, dtype=np.uint8).reshape(-1, n)
         self.bits = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)
         self.sketch = None if sketch is None else np.ascontiguousarray(sketch)
@@ -409,6 +414,7 @@ class Job:
         s.init_bits = _hptr(self.bits)
         s.n_obs, s.paulis = self.n_obs, _hptr(self.paulis)
         s.fit_method, s.fit_degree, s.lambda_star = fit_method, fit_degree, lambda_star
+        s.pauli_rates = _hptr(self.pauli)
         self.struct = s
         self.gate_steps = int(self.layer_gates.sum()) * self.n_lambda
 

@@ -81,6 +81,23 @@ def job_for(w, chi=None, dtype: int = nne.C64, trunc: int = nne.TRUNC_EXACT, ske
                    fit_method=fit, fit_degree=degree, lambda_star=w.lambda_star)
 
 
+def pauli_job(pc, lambdas, chi: int, paulis: np.ndarray, dtype: int = nne.C64, trunc: int = nne.TRUNC_EXACT,
+              sketch=None, power_iters: int = 1, bits=None, fit_method: int = nne.FIT_EXP_LOGLIN,
+              fit_degree: int = 2, lambda_star: float = 1.0) -> nne.Job:
+    """A server job for a circuit with gate-dependent Pauli channels (c0 +
+    lambda c1 per gate), in the snake schedule of build_pauli_layers."""
+    layers, pr = [], []
+    for t, (qs, us) in enumerate(zip(pc.layers, pc.unitaries)):
+        if len(qs) == 0:
+            continue
+        order = slice(None) if t % 2 == 0 else slice(None, None, -1)
+        layers.append((list(qs)[order], np.asarray(us)[order], +1 if t % 2 == 0 else -1))
+        pr.append(np.stack([np.asarray(pc.c0[t])[order], np.asarray(pc.c1[t])[order]], axis=1))
+    return nne.Job(pc.n, layers, np.asarray(lambdas, np.float64), None, chi, paulis, dtype=dtype, trunc=trunc,
+                   sketch=sketch, power_iters=power_iters, bits=bits, fit_method=fit_method, fit_degree=fit_degree,
+                   lambda_star=lambda_star, pauli=np.concatenate(pr) if pr else np.zeros((0, 2, 16)))
+
+
 def emulate_ladder(ctx: nne.Context, circuit, rates: np.ndarray, chis, paulis: np.ndarray, dtype: int = nne.C64,
                    trunc: int = nne.TRUNC_EXACT, bits=None, layers=None):
     """The same circuit at every noise level for each bond dimension of a ladder

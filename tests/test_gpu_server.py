@@ -160,3 +160,28 @@ def test_batch_subsample_vs_oracle(ctx):
         # log F sums one complex64-rounded log f per gate (about 1e-5 each): the bound grows with the gates
         assert abs(r["log_fid"][0] - ref.log_fid) < 2e-5 * w.circuit.n_gates
         assert r["gate_steps"] == w.circuit.n_gates * len(w.lambdas)
+
+
+def test_server_pauli_noise_jobs(ctx):
+    """Cat-qubit and XY-model circuits through nne_submit: identical to the
+    direct path (same kernels) and to the oracle VMPO within 1e-8 (complex128)."""
+    from oracle import channels as ch
+    from paper_2501_13237_gb300 import nne, runner
+    cases = [(wl.cat_circuit(10, 24, 7), (0.005, 0.02), 4, None),
+             (wl.xym_circuit(10, 5, dt=0.3), (0.01, 0.05), 6, wl.neel_bits(10))]
+    paulis = wl.pauli_codes(wl.obs_z(10) + wl.obs_xx(10), 10)
+    jobs = [runner.pauli_job(pc, lams, chi, paulis, dtype=nne.C128, bits=bits) for pc, lams, chi, bits in cases]
+    srv = nne.Server(0, workers=2)
+    res = [srv.poll(srv.submit(j)) for j in jobs]
+    srv.close()
+    for (pc, lams, chi, bits), j, r in zip(cases, jobs, res):
+        assert r["status"] == 0, r["error"]
+        assert r["gate_steps"] == j.gate_steps
+        layers = runner.build_pauli_layers(ctx, pc, np.asarray(lams))
+        st, vals, lf = runner.emulate(ctx, pc, None, chi, paulis, nne.C128, bits=bits, layers=layers)
+        st.close()
+        assert np.array_equal(r["values"], vals.real)
+        assert np.array_equal(r["log_fid"], lf)
+        for i, lam in enumerate(lams):
+            ref = mps.run(pc, None, chi, bits=bits, Gs=ch.pauli_superops_for(pc, lam))
+            assert np.abs(r["values"][i] - ref.expect_codes(paulis).real).max() < 1e-8

@@ -103,3 +103,35 @@ def test_destroy_drops_queued_jobs():
     t0 = time.time()
     srv.close()                      # finishes the running job only
     assert time.time() - t0 < 0.35
+
+
+def _pauli_job(lambdas=(0.005, 0.02), **kw):
+    pc = wl.cat_circuit(8, 4, 2)
+    return runner.pauli_job(pc, lambdas, 8, wl.pauli_codes(wl.obs_z(8), 8), **kw)
+
+
+def test_pauli_noise_job_is_admitted_and_sized():
+    job = _pauli_job()
+    gates = int(job.layer_gates.sum())
+    assert job.struct.rates is None and job.pauli.shape == (gates, 2, 16)
+    # the staged Pauli table (32 doubles per gate plus the levels) replaces the 4 rates per level
+    srv = nne.Server(workers=1, dry_run=True, dry_run_us=1000)
+    r = srv.poll(srv.submit(job))
+    srv.close()
+    assert r["status"] == -7 and r["bytes"] == job.bytes() > 0
+
+
+def test_pauli_noise_job_argument_checks():
+    bad = _pauli_job()
+    bad.pauli[3, 1, 0] += 0.5            # probabilities of gate 3 no longer sum to one
+    srv = nne.Server(workers=1, dry_run=True, dry_run_us=1000)
+    with pytest.raises(nne.NNEError):
+        srv.submit(bad)
+    neg = _pauli_job(lambdas=(0.005, 0.5))   # p_II = 1 - 5 lambda < 0 for H gates at lambda = 0.5
+    with pytest.raises(nne.NNEError):
+        srv.submit(neg)
+    none = _pauli_job()
+    none.struct.pauli_rates = None          # neither rates nor Pauli channels
+    with pytest.raises(nne.NNEError):
+        srv.submit(none)
+    srv.close()
