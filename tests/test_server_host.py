@@ -135,3 +135,23 @@ def test_pauli_noise_job_argument_checks():
     with pytest.raises(nne.NNEError):
         srv.submit(none)
     srv.close()
+
+
+def test_pauli_job_follows_the_snake_schedule():
+    """Gate order, directions and per-gate Pauli tables of a Pauli-noise job:
+    even layers left to right, odd layers reversed, tables travelling with
+    their gates (the order build_pauli_layers applies them in)."""
+    pc = wl.cat_circuit(7, 5, 9)
+    job = runner.pauli_job(pc, (0.01,), 8, wl.pauli_codes(wl.obs_z(7), 7))
+    off = 0
+    for t, qs in enumerate(pc.layers):
+        g = len(qs)
+        order = list(range(g)) if t % 2 == 0 else list(range(g - 1, -1, -1))
+        assert job.layer_dir[t] == (1 if t % 2 == 0 else -1) and job.layer_gates[t] == g
+        for k, i in enumerate(order):
+            assert job.left[off + k] == qs[i]
+            assert np.array_equal(job.U[off + k], pc.unitaries[t][i])
+            assert np.array_equal(job.pauli[off + k, 0], pc.c0[t][i])
+            assert np.array_equal(job.pauli[off + k, 1], pc.c1[t][i])
+        off += g
+    assert off == pc.n_gates
