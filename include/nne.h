@@ -174,7 +174,7 @@ nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* r
  * in the state's precision, and S is summed in FP64.  The state itself is
  * unchanged; its centre ends on site n-1.  S_max (App. A.1) is the maximum of
  * a row.
- *   S_out host double n_inst x (n-1), row-major: S_out[i * (n-1) + k] is the
+ *   S_out host double n_inst x (n-1), caller-owned, row-major: S_out[i * (n-1) + k] is the
  *         entropy of instance i at the bond between qubits k and k+1.
  * The Gram matrices are formed in the state's precision, so squared Schmidt
  * values below about machine epsilon times the largest are not resolved
