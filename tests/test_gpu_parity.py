@@ -225,3 +225,18 @@ def test_serial_layers_option_matches_sub_batches(ctx):
     assert np.abs(out[0][0] - out[1][0]).max() < 1e-4
     assert np.abs(out[0][1] - out[1][1]).max() < 1e-4
     assert (out[0][1] < -1e-4).all()          # truncation happens (bond 256 < 4^5)
+
+
+def test_non_finite_state_reports_noconv(ctx):
+    """A non-finite centre norm ends in NNE_ERR_NOCONV at the next sync (the
+    gate bookkeeping's own check; nothing traps): a NaN site written on the
+    host, one gate on it (bond 1, so the untruncated identity branch runs)."""
+    from paper_2501_13237_gb300 import nne
+    st = nne.State(ctx, 6, 8, 2, 1)
+    st.write_site(0, 2, np.full((1, 4, 1), np.nan, complex))
+    G = ctx.build_superops(np.stack([np.eye(4, dtype=complex)]), np.zeros((2, 4)))
+    st.apply_layer([2], G, +1)
+    with pytest.raises(nne.NNEError) as e:
+        st.sync()
+    assert e.value.status == -4
+    st.close()
