@@ -287,6 +287,12 @@ nne_status nne_state_info(nne_state* st, int* dims_out, int* centre_out, double*
 nne_status nne_state_read_site(nne_state* st, int inst, int k, void* host_out, size_t cap_bytes);
 nne_status nne_state_write_site(nne_state* st, int inst, int k, int dl, int dr, const void* host_in);
 nne_status nne_state_set_centre(nne_state* st, int centre);
+/* Overwrite the accumulated log-norm and log F of every instance (host
+ * double[n_inst] each, caller-owned; NULL leaves that one unchanged).  With
+ * nne_state_info, nne_state_read_site / nne_state_write_site and
+ * nne_state_set_centre this checkpoints and restores a state (no counterpart
+ * in the paper).  Synchronises; NNE_ERR_ARG for a null state. */
+nne_status nne_state_set_log(nne_state* st, const double* log_norm, const double* log_fid);
 
 /* Instrumentation (no counterpart in the paper).
  * nne_kernel_launches: number of CUDA kernels this library has launched in

@@ -1174,4 +1174,14 @@ nne_status nne_state_set_centre(nne_state* st, int centre) {
   return NNE_OK;
 }
 
+nne_status nne_state_set_log(nne_state* st, const double* log_norm, const double* log_fid) {
+  if (!st) return set_error(NNE_ERR_ARG, "nne_state_set_log: null state");
+  DeviceGuard dg(st->ctx->device);
+  const size_t b = sizeof(double) * st->n_inst;
+  if (log_norm) NNE_CUDA_TRY(cudaMemcpyAsync(st->d_lognorm, log_norm, b, cudaMemcpyHostToDevice, st->ctx->stream));
+  if (log_fid) NNE_CUDA_TRY(cudaMemcpyAsync(st->d_logfid, log_fid, b, cudaMemcpyHostToDevice, st->ctx->stream));
+  NNE_CUDA_TRY(cudaStreamSynchronize(st->ctx->stream));
+  return NNE_OK;
+}
+
 }  // extern "C"

@@ -31,7 +31,7 @@ SYMBOLS = (
     "nne_state_set_centre", "nne_reset_state", "nne_kernel_launches", "nne_prof_enable", "nne_prof_collect",
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
     "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
-    "nne_extrapolate_ladder", "nne_entropy", "nne_build_pauli_superops",
+    "nne_extrapolate_ladder", "nne_entropy", "nne_build_pauli_superops", "nne_state_set_log",
 )
 SERVER_DRYRUN = 1
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "nne_state_read_site": (i32, [vp, i32, i32, vp, sz]),
         "nne_state_write_site": (i32, [vp, i32, i32, i32, i32, vp]),
         "nne_state_set_centre": (i32, [vp, i32]),
+        "nne_state_set_log": (i32, [vp, vp, vp]),
         "nne_reset_state": (i32, [vp, vp]),
         "nne_kernel_launches": (C.c_longlong, []),
         "nne_prof_enable": (None, [i32]),
@@ -348,6 +349,26 @@ class State:
 
     def set_centre(self, c: int):
         _check(load().nne_state_set_centre(self.h, c))
+
+    def set_log(self, log_norm=None, log_fid=None):
+        ln = None if log_norm is None else np.ascontiguousarray(log_norm, dtype=np.float64)
+        lf = None if log_fid is None else np.ascontiguousarray(log_fid, dtype=np.float64)
+        _check(load().nne_state_set_log(self.h, _hptr(ln), _hptr(lf)))
+
+    def checkpoint(self) -> dict:
+        """Host copy of the whole state: bond dims, centre, log-norm, log F and
+        every site tensor of every instance."""
+        dims, centre, ln, lf = self.info()
+        sites = [[self.read_site(i, k) for k in range(self.n)] for i in range(self.n_inst)]
+        return {"dims": dims, "centre": centre, "log_norm": ln, "log_fid": lf, "sites": sites}
+
+    def restore(self, ck: dict):
+        """Load a checkpoint of a state with the same n, chi, n_inst and dtype."""
+        for i, row in enumerate(ck["sites"]):
+            for k, M in enumerate(row):
+                self.write_site(i, k, M)
+        self.set_centre(int(ck["centre"]))
+        self.set_log(ck["log_norm"], ck["log_fid"])
 
     def reset(self, bits=None):
         b = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)

@@ -240,3 +240,31 @@ def test_non_finite_state_reports_noconv(ctx):
         st.sync()
     assert e.value.status == -4
     st.close()
+
+
+def test_checkpoint_restore_continues_bit_for_bit(ctx):
+    """A state saved after four layers (sites, bond dims, centre, log-norm,
+    log F) and restored into a fresh state continues exactly like the
+    uninterrupted one (same kernels on the same data)."""
+    from paper_2501_13237_gb300 import nne, runner
+    n, chi = 8, 16
+    c = wl.brickwork_circuit(n, 8, 41)
+    rates = np.stack([wl.NoiseModel(depol2=0.02, dephase=0.01).rates(l) for l in (1, 2)])
+    layers = runner.build_layer_superops(ctx, c, rates)
+    paulis = wl.pauli_codes(wl.obs_z(n) + wl.obs_xx(n), n)
+    for dtype in (0, 1):
+        a = nne.State(ctx, n, chi, 2, dtype)
+        runner.evolve(a, layers[:4])
+        ck = a.checkpoint()
+        runner.evolve(a, layers[4:])
+        va, lfa = a.expect(paulis)
+        a.close()
+        b = nne.State(ctx, n, chi, 2, dtype)
+        b.restore(ck)
+        dims, centre, ln, lf = b.info()
+        assert np.array_equal(dims, ck["dims"]) and centre == ck["centre"] and np.array_equal(lf, ck["log_fid"])
+        runner.evolve(b, layers[4:])
+        vb, lfb = b.expect(paulis)
+        b.close()
+        assert np.array_equal(va, vb) and np.array_equal(lfa, lfb)
+        assert (lfa < -1e-6).all()
