@@ -394,6 +394,13 @@ void nne_server_stats(nne_server* srv, int* queued, int* running, int* done, siz
 /* Finishes the running jobs, drops the queued ones, joins the workers. */
 void nne_server_destroy(nne_server* srv);
 
+/* Metrics log (no counterpart in the paper): append one JSON line per finished
+ * job to the file at path -- ticket, status, error, n, chi, n_lambda, gates,
+ * gate_steps, bytes, t_submit, t_start, t_end, latency_s (seconds on the
+ * server's clock) and log_fid (log F per level, empty when the job produced
+ * none).  NULL path stops logging.  NNE_ERR_ARG if the file cannot be opened. */
+nne_status nne_server_set_log(nne_server* srv, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -74,11 +75,35 @@ struct nne_server {
   bool stop = false;
   uint64_t next_ticket = 1;
   std::vector<std::thread> workers;
+  FILE* log = nullptr;   // JSON-lines record of finished jobs (nne_server_set_log), guarded by mu
   Clock::time_point t0 = Clock::now();
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
 namespace {
+
+// One JSON line per finished job (called with the server mutex held).
+void log_job(FILE* f, const JobCopy& j, const ResultRec& r) {
+  std::string err;
+  for (char c : r.error) {
+    if (c == '"' || c == '\\') err += '\\';
+    if (static_cast<unsigned char>(c) >= 0x20) err += c;
+  }
+  std::fprintf(f,
+               "{\"ticket\": %llu, \"status\": %d, \"error\": \"%s\", \"n\": %d, \"chi\": %d, "
+               "\"n_lambda\": %d, \"gates\": %lld, \"gate_steps\": %lld, \"bytes\": %zu, "
+               "\"t_submit\": %.6f, \"t_start\": %.6f, \"t_end\": %.6f, \"latency_s\": %.6f, \"log_fid\": [",
+               (unsigned long long)j.ticket, (int)r.status, err.c_str(), j.n, j.chi, j.n_lambda, j.gates,
+               r.gate_steps, r.bytes, r.t_submit, r.t_start, r.t_end, r.t_end - r.t_submit);
+  for (size_t i = 0; i < r.log_fid.size(); ++i) {
+    if (std::isfinite(r.log_fid[i]))
+      std::fprintf(f, "%s%.17g", i ? ", " : "", r.log_fid[i]);
+    else
+      std::fprintf(f, "%snull", i ? ", " : "");
+  }
+  std::fprintf(f, "]}\n");
+  std::fflush(f);
+}
 
 nne_status run_job(nne_ctx* ctx, cudaStream_t st, const JobCopy& j, ResultRec& r) {
   nne_state* s = nullptr;
@@ -204,6 +229,7 @@ void worker_main(nne_server* srv) {
       res->error = err;
       res->t_end = srv->now();
       res->done = true;
+      if (srv->log) log_job(srv->log, *job, *res);
       srv->reserved -= job->bytes;
       srv->running--;
     }
@@ -410,7 +436,18 @@ void nne_server_destroy(nne_server* srv) {
   }
   srv->cv_work.notify_all();
   for (auto& t : srv->workers) t.join();
+  if (srv->log) std::fclose(srv->log);
   delete srv;
+}
+
+nne_status nne_server_set_log(nne_server* srv, const char* path) {
+  if (!srv) return nne::set_error(NNE_ERR_ARG, "nne_server_set_log: null server");
+  FILE* f = nullptr;
+  if (path && !(f = std::fopen(path, "a"))) return nne::set_error(NNE_ERR_ARG, "nne_server_set_log: cannot open %s", path);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->log) std::fclose(srv->log);
+  srv->log = f;
+  return NNE_OK;
 }
 
 }  // extern "C"

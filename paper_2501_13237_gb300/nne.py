@@ -32,6 +32,7 @@ SYMBOLS = (
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
     "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
     "nne_extrapolate_ladder", "nne_entropy", "nne_build_pauli_superops", "nne_state_set_log",
+    "nne_server_set_log",
 )
 SERVER_DRYRUN = 1
 
@@ -110,6 +111,7 @@ def load(path: str = LIB_PATH):
         "nne_poll": (i32, [vp, C.c_uint64, i32, P(ResultStruct)]),
         "nne_server_stats": (None, [vp, P(i32), P(i32), P(i32), P(sz)]),
         "nne_server_destroy": (None, [vp]),
+        "nne_server_set_log": (i32, [vp, C.c_char_p]),
         "nne_extrapolate_ladder": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -448,13 +450,19 @@ class Server:
     under a device-memory budget).  dry_run: queueing only, no GPU work."""
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, workers: int = 2, dry_run: bool = False,
-                 dry_run_us: int = 0):
+                 dry_run_us: int = 0, log_path: Optional[str] = None):
         L = load()
         h = C.c_void_p()
         _check(L.nne_server_create(device, hbm_budget_bytes, workers, SERVER_DRYRUN if dry_run else 0,
                                    dry_run_us, C.byref(h)))
         self.h = h
         self.jobs = {}
+        if log_path is not None:
+            self.set_log(log_path)
+
+    def set_log(self, path: Optional[str]):
+        """Append one JSON line per finished job to path (None: stop)."""
+        _check(load().nne_server_set_log(self.h, None if path is None else path.encode()))
 
     def close(self):
         if self.h:

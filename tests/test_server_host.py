@@ -155,3 +155,29 @@ def test_pauli_job_follows_the_snake_schedule():
             assert np.array_equal(job.pauli[off + k, 1], pc.c1[t][i])
         off += g
     assert off == pc.n_gates
+
+
+def test_metrics_log_jsonl(tmp_path):
+    """nne_server_set_log: one JSON line per finished job with its ticket,
+    status, sizes and times (latency = end - submit, on the server clock)."""
+    import json
+    path = tmp_path / "jobs.jsonl"
+    srv = nne.Server(workers=2, dry_run=True, dry_run_us=20000, log_path=str(path))
+    jobs = [_job(seed=i, lambdas=(1.0, 2.0, 3.0)) for i in range(3)]
+    tickets = [srv.submit(j) for j in jobs]
+    res = [srv.poll(t) for t in tickets]
+    srv.set_log(None)                   # stop logging; later jobs leave no line
+    srv.poll(srv.submit(_job()))
+    srv.close()
+    lines = [json.loads(l) for l in path.read_text().splitlines()]
+    assert sorted(l["ticket"] for l in lines) == sorted(tickets)
+    for l in lines:
+        r = res[tickets.index(l["ticket"])]
+        assert l["status"] == -7 and l["error"] == "dry run: no GPU work"
+        assert (l["n"], l["chi"], l["n_lambda"]) == (8, 16, 3) and l["gates"] == int(jobs[0].layer_gates.sum())
+        assert l["bytes"] == r["bytes"] and l["log_fid"] == []
+        assert l["t_submit"] <= l["t_start"] <= l["t_end"]
+        assert abs(l["latency_s"] - (l["t_end"] - l["t_submit"])) < 1e-5
+        assert abs(l["t_end"] - r["t_end"]) < 1e-5
+    with pytest.raises(nne.NNEError):
+        nne.Server(workers=1, dry_run=True, log_path=str(tmp_path / "missing" / "x.jsonl"))
