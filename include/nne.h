@@ -56,6 +56,7 @@ typedef int32_t nne_status;
 #define NNE_ERR_TIMEOUT (-5)
 #define NNE_ERR_NOFIT (-6)
 #define NNE_ERR_UNIMPL (-7)
+#define NNE_ERR_CANCELLED (-8)
 
 typedef enum { NNE_C64 = 0, NNE_C128 = 1 } nne_dtype;
 
@@ -400,6 +401,13 @@ void nne_server_destroy(nne_server* srv);
  * server's clock) and log_fid (log F per level, empty when the job produced
  * none).  NULL path stops logging.  NNE_ERR_ARG if the file cannot be opened. */
 nne_status nne_server_set_log(nne_server* srv, const char* path);
+
+/* Cancel a request.  A job still waiting in the queue is removed and its
+ * result completes at once with status NNE_ERR_CANCELLED (collect it with
+ * nne_poll as usual).  A running job is not interrupted: the call returns
+ * NNE_PENDING and the job completes normally.  NNE_ERR_ARG for an unknown or
+ * already finished ticket. */
+nne_status nne_cancel(nne_server* srv, uint64_t ticket);
 
 #ifdef __cplusplus
 }

@@ -9,6 +9,7 @@
 // Every job runs through the public entry points (nne_create_state,
 // nne_build_superops, nne_apply_layer, nne_expect, nne_extrapolate); this
 // file holds no arithmetic of the method.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -413,6 +414,30 @@ nne_status nne_poll(nne_server* srv, uint64_t ticket, int timeout_ms, nne_result
   out->gate_steps = r->gate_steps;
   out->bytes_reserved = r->bytes;
   srv->results.erase(it);
+  return NNE_OK;
+}
+
+nne_status nne_cancel(nne_server* srv, uint64_t ticket) {
+  if (!srv) return nne::set_error(NNE_ERR_ARG, "nne_cancel: null server");
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->results.find(ticket);
+    if (it == srv->results.end() || it->second->done)
+      return nne::set_error(NNE_ERR_ARG, "nne_cancel: unknown or finished ticket %llu", (unsigned long long)ticket);
+    auto q = std::find_if(srv->queue.begin(), srv->queue.end(),
+                          [&](const std::shared_ptr<JobCopy>& j) { return j->ticket == ticket; });
+    if (q == srv->queue.end()) return NNE_PENDING;   // running: it completes normally
+    std::shared_ptr<JobCopy> job = *q;
+    srv->queue.erase(q);
+    ResultRec& r = *it->second;
+    r.status = NNE_ERR_CANCELLED;
+    r.error = "cancelled before it started";
+    r.t_start = r.t_end = srv->now();
+    r.done = true;
+    if (srv->log) log_job(srv->log, *job, r);
+  }
+  srv->cv_done.notify_all();
+  srv->cv_work.notify_all();   // the queue head may have changed
   return NNE_OK;
 }
 

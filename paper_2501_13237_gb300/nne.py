@@ -17,7 +17,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libnne.so")
 
 OK, PENDING = 0, 1
-ERR = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NOCONV", -5: "TIMEOUT", -6: "NOFIT", -7: "UNIMPL"}
+ERR = {-1: "ARG", -2: "OOM", -3: "CUDA", -4: "NOCONV", -5: "TIMEOUT", -6: "NOFIT", -7: "UNIMPL", -8: "CANCELLED"}
+ERR_CANCELLED = -8
 C64, C128 = 0, 1
 TRUNC_EXACT, TRUNC_RSVD = 0, 1
 FIT_POLY, FIT_EXP_LOGLIN, FIT_EXP3 = 0, 1, 2
@@ -32,7 +33,7 @@ SYMBOLS = (
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
     "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
     "nne_extrapolate_ladder", "nne_entropy", "nne_build_pauli_superops", "nne_state_set_log",
-    "nne_server_set_log",
+    "nne_server_set_log", "nne_cancel",
 )
 SERVER_DRYRUN = 1
 
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
         "nne_server_stats": (None, [vp, P(i32), P(i32), P(i32), P(sz)]),
         "nne_server_destroy": (None, [vp]),
         "nne_server_set_log": (i32, [vp, C.c_char_p]),
+        "nne_cancel": (i32, [vp, C.c_uint64]),
         "nne_extrapolate_ladder": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -459,6 +461,15 @@ class Server:
         self.jobs = {}
         if log_path is not None:
             self.set_log(log_path)
+
+    def cancel(self, ticket: int) -> bool:
+        """Cancel a queued request (True); False if it is already running and
+        will complete normally.  Raises for an unknown or finished ticket."""
+        rc = load().nne_cancel(self.h, C.c_uint64(ticket))
+        if rc == PENDING:
+            return False
+        _check(rc)
+        return True
 
     def set_log(self, path: Optional[str]):
         """Append one JSON line per finished job to path (None: stop)."""

@@ -181,3 +181,30 @@ def test_metrics_log_jsonl(tmp_path):
         assert abs(l["t_end"] - r["t_end"]) < 1e-5
     with pytest.raises(nne.NNEError):
         nne.Server(workers=1, dry_run=True, log_path=str(tmp_path / "missing" / "x.jsonl"))
+
+
+def test_cancel_queued_and_running_requests(tmp_path):
+    """nne_cancel: a queued job completes at once as cancelled and frees its
+    place in the queue; a running job is not interrupted; finished or unknown
+    tickets are refused."""
+    import json
+    log = tmp_path / "jobs.jsonl"
+    srv = nne.Server(workers=1, dry_run=True, dry_run_us=150000, log_path=str(log))
+    t = [srv.submit(_job(seed=i)) for i in range(3)]
+    while srv.stats()["running"] == 0:
+        time.sleep(0.005)
+    assert srv.cancel(t[1]) is True                 # still queued
+    r1 = srv.poll(t[1], timeout_ms=0)
+    assert r1["status"] == nne.ERR_CANCELLED and r1["t_start"] == r1["t_end"]
+    assert srv.cancel(t[0]) is False                # running: completes normally
+    res = [srv.poll(t[0]), srv.poll(t[2])]
+    assert [r["status"] for r in res] == [-7, -7]
+    assert res[1]["t_start"] >= res[0]["t_end"] - 1e-6     # the cancelled job never ran in between
+    assert res[1]["t_start"] - res[0]["t_start"] < 0.28     # one dry-run period (0.15 s), not two
+    with pytest.raises(nne.NNEError):
+        srv.cancel(t[2])                            # finished (and collected)
+    with pytest.raises(nne.NNEError):
+        srv.cancel(987654)
+    srv.close()
+    lines = {l["ticket"]: l for l in map(json.loads, log.read_text().splitlines())}
+    assert lines[t[1]]["status"] == nne.ERR_CANCELLED and set(lines) == set(t)
