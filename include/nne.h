@@ -409,6 +409,14 @@ nne_status nne_server_set_log(nne_server* srv, const char* path);
  * already finished ticket. */
 nne_status nne_cancel(nne_server* srv, uint64_t ticket);
 
+/* Fault injection for tests of failure handling (no counterpart in the
+ * paper; host only, no GPU fault): the waiting job with this ticket, when a
+ * worker takes it, ends with `status` (a negative nne_status) and error
+ * "injected failure" instead of running; its memory reservation is released as
+ * for any finished job.  NNE_ERR_ARG for a non-negative status or a ticket
+ * that is not waiting in the queue. */
+nne_status nne_server_inject_failure(nne_server* srv, uint64_t ticket, nne_status status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,7 @@ struct nne_server {
   uint64_t next_ticket = 1;
   std::vector<std::thread> workers;
   FILE* log = nullptr;   // JSON-lines record of finished jobs (nne_server_set_log), guarded by mu
+  std::unordered_map<uint64_t, nne_status> injected;   // nne_server_inject_failure, guarded by mu
   Clock::time_point t0 = Clock::now();
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
@@ -193,6 +194,7 @@ void worker_main(nne_server* srv) {
       init_err = nne_last_error();
     }
   }
+  nne_status injected_rc = NNE_OK;
   for (;;) {
     std::shared_ptr<JobCopy> job;
     std::shared_ptr<ResultRec> res;
@@ -210,10 +212,19 @@ void worker_main(nne_server* srv) {
       res = srv->results[job->ticket];
       res->t_start = srv->now();
       res->bytes = job->bytes;
+      auto inj = srv->injected.find(job->ticket);
+      if (inj != srv->injected.end()) {
+        injected_rc = inj->second;
+        srv->injected.erase(inj);
+      }
     }
     nne_status rc;
     std::string err;
-    if (dry) {
+    if (injected_rc != NNE_OK) {
+      rc = injected_rc;
+      err = "injected failure";
+      injected_rc = NNE_OK;
+    } else if (dry) {
       std::this_thread::sleep_for(std::chrono::microseconds(srv->dry_us));
       rc = NNE_ERR_UNIMPL;
       err = "dry run: no GPU work";
@@ -414,6 +425,17 @@ nne_status nne_poll(nne_server* srv, uint64_t ticket, int timeout_ms, nne_result
   out->gate_steps = r->gate_steps;
   out->bytes_reserved = r->bytes;
   srv->results.erase(it);
+  return NNE_OK;
+}
+
+nne_status nne_server_inject_failure(nne_server* srv, uint64_t ticket, nne_status status) {
+  if (!srv || status >= 0) return nne::set_error(NNE_ERR_ARG, "nne_server_inject_failure: bad arguments");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->results.find(ticket);
+  if (it == srv->results.end() || it->second->done || it->second->t_start > 0)
+    return nne::set_error(NNE_ERR_ARG, "nne_server_inject_failure: ticket %llu is not waiting",
+                          (unsigned long long)ticket);
+  srv->injected[ticket] = status;
   return NNE_OK;
 }
 

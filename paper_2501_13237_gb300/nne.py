@@ -33,7 +33,7 @@ SYMBOLS = (
     "nne_extrapolate_noalloc", "nne_cgemm_c64", "nne_set_option",
     "nne_server_create", "nne_job_bytes", "nne_submit", "nne_poll", "nne_server_stats", "nne_server_destroy",
     "nne_extrapolate_ladder", "nne_entropy", "nne_build_pauli_superops", "nne_state_set_log",
-    "nne_server_set_log", "nne_cancel",
+    "nne_server_set_log", "nne_cancel", "nne_server_inject_failure",
 )
 SERVER_DRYRUN = 1
 
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
         "nne_server_destroy": (None, [vp]),
         "nne_server_set_log": (i32, [vp, C.c_char_p]),
         "nne_cancel": (i32, [vp, C.c_uint64]),
+        "nne_server_inject_failure": (i32, [vp, C.c_uint64, i32]),
         "nne_extrapolate_ladder": (i32, [vp, i32, i32, vp, vp, vp, i32, i32, i32, dbl, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -470,6 +471,10 @@ class Server:
             return False
         _check(rc)
         return True
+
+    def inject_failure(self, ticket: int, status: int):
+        """Test hook: the waiting job ends with `status` when a worker takes it."""
+        _check(load().nne_server_inject_failure(self.h, C.c_uint64(ticket), status))
 
     def set_log(self, path: Optional[str]):
         """Append one JSON line per finished job to path (None: stop)."""

@@ -208,3 +208,24 @@ def test_cancel_queued_and_running_requests(tmp_path):
     srv.close()
     lines = {l["ticket"]: l for l in map(json.loads, log.read_text().splitlines())}
     assert lines[t[1]]["status"] == nne.ERR_CANCELLED and set(lines) == set(t)
+
+
+def test_injected_failure_ends_only_that_job():
+    """Host-side fault injection: the chosen job ends with the injected status,
+    the others run, and every memory reservation is returned."""
+    srv = nne.Server(hbm_budget_bytes=10 * _job().bytes(), workers=1, dry_run=True, dry_run_us=60000)
+    t = [srv.submit(_job(seed=i)) for i in range(4)]
+    while srv.stats()["running"] == 0:
+        time.sleep(0.005)
+    with pytest.raises(nne.NNEError):
+        srv.inject_failure(t[0], -4)                # already running
+    with pytest.raises(nne.NNEError):
+        srv.inject_failure(t[2], 0)                 # not a failure status
+    srv.inject_failure(t[2], -4)                    # NNE_ERR_NOCONV, as a failed eigensolve reports
+    res = [srv.poll(x) for x in t]
+    assert [r["status"] for r in res] == [-7, -7, -4, -7]
+    assert res[2]["error"] == "injected failure"
+    assert res[3]["t_start"] >= res[2]["t_end"] - 1e-6      # the queue went on after the failure
+    st = srv.stats()
+    srv.close()
+    assert st["bytes_reserved"] == 0 and st["running"] == 0 and st["queued"] == 0
