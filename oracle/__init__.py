@@ -18,6 +18,8 @@ Modules
                  SVD truncation to fixed D, Frobenius normalisation, partial
                  fidelities (Sec. 2.1.1-2.1.2, eqs. for f_l and F), centre moves,
                  Pauli expectation values
+  pure_mps    -- pure-state MPS (local dimension 2) for the noise-free level
+                 lambda = 0, same schedule, truncation and gauge as mps
   matchgate   -- exact noisy expectation values of matchgate circuits under
                  Pauli noise (free-fermion covariance evolution; App. C.3)
   fit         -- noise extrapolation: polynomial, weighted log-linear and
