@@ -3,10 +3,11 @@
 
 At lambda = 0 the paper emulates the circuit as a pure state (an MPS with
 local dimension 2) at a higher bond dimension than the noisy VMPO runs
-(Sec. 2.2.3, the lambda = 0 point as the sign reference of criterion 3 and
-"approximately converged"; Sec. 3.2.1 uses D = 100 pure against D = 300
-mixed).  The algorithm is the VMPO one (oracle/mps.py) with the local space
-of one qubit instead of its vectorised density matrix:
+(Sec. 2.2.3: the lambda = 0 point is the sign reference of criterion 3 and,
+run at the higher bond dimension, is taken as converged; Sec. 3.2.1 uses
+D = 100 pure against D = 300 mixed).  The algorithm is the VMPO one
+(oracle/mps.py) with the local space of one qubit instead of its vectorised
+density matrix:
 
   * site tensors A[k] of shape (chi_k, 2, chi_{k+1}); initial basis state;
   * a gate U on (q, q+1): centre onto the pair, theta[a,s1,s2,b] =
@@ -17,8 +18,9 @@ of one qubit instead of its vectorised density matrix:
   * the snake schedule and the gauge conventions of oracle/mps.py, so that
     an accelerated implementation can be compared tensor by tensor;
   * <P> = <psi|P|psi> / <psi|psi> by a two-layer transfer-matrix sweep;
-  * bond entropies -sum p ln p of the squared Schmidt values (the "usual"
-    entanglement entropy the paper shows at lambda = 0, Sec. 2.2).
+  * bond entropies -sum p ln p of the squared Schmidt values (the ordinary
+    entanglement entropy of a pure state, which the paper plots at
+    lambda = 0, Sec. 2.2).
 
 Pins (tests/test_oracle_pure_mps.py): untruncated runs equal the statevector;
 after a single truncation the true fidelity |<psi_exact|psi>|^2 equals the
