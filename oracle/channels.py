@@ -20,8 +20,7 @@ channel C; here C is the composition, in this order, of
   3. dephasing p_z on each qubit (K0 = sqrt(1-p_z) I, K1 = sqrt(p_z) Z),
   4. single-qubit depolarizing with error probability p1 on each qubit
      (K0 = sqrt(1-p1) I, sqrt(p1/3){X,Y,Z}; <Z> -> (1 - 4 p1/3) <Z>).
-The order of 2-4 is a reading (the paper never composes channels); it is
-stated in DESIGN.md.
+The order of 2-4 is a reading: the paper never composes channels.
 
 Gate-dependent Pauli channels (cat-qubit noise, App. C.2.2; matchgate
 depolarizing noise, App. C.3.1) are built by kraus_pauli from 16

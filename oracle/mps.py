@@ -8,8 +8,8 @@ Initial state: the product |b><b| (Sec. 2.1.2: the initial state is always a
 product state, so rho~_0 = rho_0), all bond dimensions 1.
 
 One subcircuit = one gate and its channel on (q, q+1) (the granularity of
-the paper's partial fidelities is left open; this reading is stated in
-DESIGN.md).  Each subcircuit (Sec. 2.1.2 "Approximate emulation"):
+the paper's partial fidelities is left open, so this is a reading of
+Sec. 2.1.2).  Each subcircuit (Sec. 2.1.2 "Approximate emulation"):
   1. move the orthogonality centre onto the pair (QR / LQ steps; canonical
      form of App. A.1, footnote on bond-local Schmidt values);
   2. theta[a,s1,s2,b] = sum_c M[q][a,s1,c] M[q+1][c,s2,b];
@@ -29,7 +29,7 @@ DESIGN.md).  Each subcircuit (Sec. 2.1.2 "Approximate emulation"):
      (eq. emulation_fidelity).
 Direction +1 (left to right): the left factor U_r stays on q, the centre
 S_r V_r^dagger moves to q+1.  Direction -1: V_r^dagger stays on q+1, the
-centre U_r S_r moves to q.  Brickwork schedule (a reading): even
+centre U_r S_r moves to q.  Brickwork schedule (a reading: the paper fixes none): even
 layers left to right, odd layers right to left.
 
 Expectation values (Sec. 2.2.3, <O>_lambda; exact contraction of the tensor
@@ -38,14 +38,10 @@ network): <P> = Tr(P rho~) / Tr(rho~) with per-site vectors v_P[s] = P[j, i].
 Gauge convention (shared with the GPU path so that site tensors are unique):
 QR factors have a real non-negative R diagonal; every truncation isometry
 (columns ordered by decreasing weight) has each column scaled so its column
-sum is real and non-negative.  Observables do not depend on it; the
-randomized variant below does (its sketch acts in the current bond basis).
+sum is real and non-negative.  Observables do not depend on it.
 
-Randomized variant (a design choice of the GPU path, not the paper's): the
-kept subspace may instead come from the randomized range finder with a
-given sketch matrix (range_finder_isometry); it equals the SVD truncation
-whenever the sketch covers the rank bound, and otherwise keeps a subspace
-whose captured weight is at most the optimal one.
+The truncation here is always the exact SVD truncation of the paper; how a
+fast implementation reaches the same kept subspace is not modelled.
 
 Pins (tests/test_oracle_mps.py): untruncated runs equal the dense simulator
 to 1e-12 (n <= 8); lambda = 0 equals the statevector; truncated runs equal an
@@ -89,11 +85,9 @@ def qr_fixed(M: np.ndarray):
 
 
 class VMPO:
-    def __init__(self, n: int, chi: int, bits=None, sketch: np.ndarray = None, power_iters: int = 0):
+    def __init__(self, n: int, chi: int, bits=None):
         self.n = n
         self.chi = chi
-        self.sketch = sketch
-        self.power_iters = power_iters
         bits = [0] * n if bits is None else [int(b) for b in bits]
         self.M: List[np.ndarray] = []
         for b in bits:
@@ -134,8 +128,7 @@ class VMPO:
     # ------------------------------------------------------------- gate step
     def gate(self, q: int, G: np.ndarray, direction: int):
         self.move_centre(q if direction > 0 else q + 1)
-        left, right, f, nrm, s = two_site_update(self.M[q], self.M[q + 1], G, self.chi, direction,
-                                                 self.sketch, self.power_iters)
+        left, right, f, nrm, s = two_site_update(self.M[q], self.M[q + 1], G, self.chi, direction)
         self.M[q], self.M[q + 1] = left, right
         self.centre = q + 1 if direction > 0 else q
         self.log_norm += math.log(nrm)
@@ -249,32 +242,8 @@ def theta_superop(A: np.ndarray, B: np.ndarray, G: np.ndarray) -> np.ndarray:
     return thetap.reshape(cl * 4, 4 * cr)
 
 
-def range_finder_isometry(A: np.ndarray, r: int, omega: np.ndarray, q: int) -> np.ndarray:
-    """Top-r left singular subspace of A (n x m) by the randomized range finder:
-    Y = A Omega (k columns), q power iterations Q <- orth(A (A^H Q)),
-    Rayleigh-Ritz on C = (Q^H A)(Q^H A)^H, W = Q * (top-r eigenvectors of C)
-    (Halko, Martinsson & Tropp 2011, Algs. 4.4 and 5.1).  When k >= n the sketch
-    spans the whole space and the exact top-r eigenvectors of A A^H are returned."""
-    n, m = A.shape
-    k = omega.shape[1]
-    if k >= n or k < r:
-        ev, V = np.linalg.eigh(A @ A.conj().T)
-        return fix_columns(V[:, ::-1][:, :r])
-    Q, _ = np.linalg.qr(A @ omega[:m, :k])
-    for _ in range(q):
-        Q, _ = np.linalg.qr(A @ (A.conj().T @ Q))
-    Bm = Q.conj().T @ A
-    ev, V = np.linalg.eigh(Bm @ Bm.conj().T)
-    return fix_columns(Q @ V[:, ::-1][:, :r])
-
-
-def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direction: int,
-                    sketch: np.ndarray = None, power_iters: int = 0):
+def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direction: int):
     """One subcircuit on a pair in canonical form (steps 2-6 of the module header).
-
-    With a sketch matrix the kept subspace comes from the randomized range finder
-    (range_finder_isometry) instead of the exact SVD; the split, normalisation and
-    f_l bookkeeping are the same.
     Returns (new_left, new_right, f, norm_of_kept_part, singular_values)."""
     cl, cr = A.shape[0], B.shape[2]
     X = theta_superop(A, B, G)
@@ -296,20 +265,6 @@ def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direc
         Q, Rm = qr_fixed(X.conj().T)
         nrm = float(np.linalg.norm(Rm))
         return (Rm.conj().T / nrm).reshape(cl, 4, r), Q.conj().T.reshape(r, 4, cr), 1.0, nrm, S
-    if sketch is not None:
-        S = np.linalg.svd(X, compute_uv=False)
-        total = float(np.sum(np.abs(X) ** 2))
-        if direction > 0:
-            Ur = range_finder_isometry(X, r, sketch, power_iters)
-            C = Ur.conj().T @ X
-            kept = float(np.sum(np.abs(C) ** 2))
-            nrm = math.sqrt(kept)
-            return Ur.reshape(cl, 4, r), (C / nrm).reshape(r, 4, cr), kept / total, nrm, S
-        Vr = range_finder_isometry(X.conj().T, r, sketch, power_iters)
-        C = X @ Vr
-        kept = float(np.sum(np.abs(C) ** 2))
-        nrm = math.sqrt(kept)
-        return (C / nrm).reshape(cl, 4, r), Vr.conj().T.reshape(r, 4, cr), kept / total, nrm, S
     U, S, Vh = np.linalg.svd(X, full_matrices=False)
     total = float(np.sum(S ** 2))
     kept = float(np.sum(S[:r] ** 2))
@@ -335,9 +290,9 @@ def superops_for(circuit, rates) -> List[np.ndarray]:
             for us in circuit.unitaries]
 
 
-def run(circuit, rates, chi: int, bits=None, Gs=None, sketch=None, power_iters: int = 0) -> VMPO:
+def run(circuit, rates, chi: int, bits=None, Gs=None) -> VMPO:
     """Emulate a brickwork circuit at one noise level with the snake schedule."""
-    st = VMPO(circuit.n, chi, bits, sketch, power_iters)
+    st = VMPO(circuit.n, chi, bits)
     Gs = superops_for(circuit, rates) if Gs is None else Gs
     for t, (qs, G) in enumerate(zip(circuit.layers, Gs)):
         if len(qs) == 0:

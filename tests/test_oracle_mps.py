@@ -199,41 +199,3 @@ def test_truncate_sweep_matches_sequential_projection():
         assert abs(g - bf_expect(vec, ob, n)) < 1e-10
 
 
-# ----------------------------------------------------------- randomized truncation
-def test_range_finder_exact_when_sketch_covers_space():
-    rng = np.random.default_rng(30)
-    A = rng.standard_normal((6, 4, 5)) + 1j * rng.standard_normal((6, 4, 5))
-    B = rng.standard_normal((5, 4, 7)) + 1j * rng.standard_normal((5, 4, 7))
-    G = ch.gate_superop(wl.haar_u4(rng), RATES)
-    om = wl.gaussian_sketch(28, 24, 1)          # k = 24 = 4*6 rows: covers the space for dir > 0
-    for d in (+1, -1):
-        l1, r1, f1, n1, _ = mps.two_site_update(A, B, G, 10, d)
-        l2, r2, f2, n2, _ = mps.two_site_update(A, B, G, 10, d, sketch=wl.gaussian_sketch(28, 28, 2))
-        X1 = np.einsum("asc,ctb->astb", l1, r1).reshape(24, 28)
-        X2 = np.einsum("asc,ctb->astb", l2, r2).reshape(24, 28)
-        assert np.abs(X1 - X2).max() < 1e-12 and abs(f1 - f2) < 1e-13 and abs(n1 - n2) < 1e-12
-
-
-def test_range_finder_recovers_gapped_subspace():
-    rng = np.random.default_rng(31)
-    n, m, r = 60, 50, 8
-    U0, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
-    V0, _ = np.linalg.qr(rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m)))
-    s = np.concatenate([np.linspace(1.0, 0.5, r), 1e-7 * np.linspace(1.0, 0.1, m - r)])
-    X = (U0[:, :m] * s) @ V0.conj().T
-    W = mps.range_finder_isometry(X, r, wl.gaussian_sketch(m, 12, 3), 1)
-    P = W @ W.conj().T
-    assert np.abs(P - U0[:, :r] @ U0[:, :r].conj().T).max() < 1e-10
-    assert np.abs(W.conj().T @ W - np.eye(r)).max() < 1e-13
-
-
-def test_range_finder_kept_weight_not_above_optimal():
-    rng = np.random.default_rng(32)
-    for t in range(5):
-        X = rng.standard_normal((40, 36)) + 1j * rng.standard_normal((40, 36))
-        r = 10
-        W = mps.range_finder_isometry(X, r, wl.gaussian_sketch(36, 14, 10 + t), 1)
-        kept = np.sum(np.abs(W.conj().T @ X) ** 2)
-        S = np.linalg.svd(X, compute_uv=False)
-        assert kept <= np.sum(S[:r] ** 2) * (1 + 1e-12)
-        assert kept >= 0.8 * np.sum(S[:r] ** 2)
