@@ -241,7 +241,9 @@ nne_status nne_extrapolate_ladder(nne_ctx* ctx, int k, int n_lambda, const doubl
  * The first call on a device looks up the array's device address with that
  * device current; make that first call before any stream capture.  All calls
  * share the array: calls that overlap on the GPU race; calls made one after
- * another are safe (each call waits for its results before returning). */
+ * another are safe (each call waits for its results before returning).  The
+ * looked-up address is kept for the life of the process, so the library must
+ * not be used across a cudaDeviceReset of that device. */
 nne_status nne_extrapolate_noalloc(nne_ctx* ctx, int n_lambda, const double* lambdas, const double* values,
                                    const double* log_fid, int n_obs, int method, int degree,
                                    double lambda_star, const double* y_zero, double* out,
@@ -268,10 +270,17 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
  * NNE_OPT_SERIAL_LAYERS (default 0): when 1, nne_apply_layer runs all of a
  * state's instances as one batch on the context stream, whatever the state's
  * sub-batch count -- for per-launch timing of the kernels alone.
+ * NNE_OPT_EIG_FP64 (default 1): complex64 states solve the truncation's
+ * Hermitian eigenproblems (the Gram matrix of the exact truncation, the
+ * Rayleigh-Ritz matrix of the subspace iteration, the centre compression)
+ * with the Householder reduction, bisection and inverse iteration in float64
+ * and the back-transformation in float32; 0 runs all of it in float32 (for
+ * comparisons).  complex128 states always use float64.
  * Options are process-wide; set them while no other thread calls the library. */
 #define NNE_OPT_TENSOR_CORES 0
 #define NNE_OPT_SUBBATCHES 1
 #define NNE_OPT_SERIAL_LAYERS 2
+#define NNE_OPT_EIG_FP64 3
 void nne_set_option(int option, int value);
 
 /* Wait for the state's enqueued work; returns the first device-side error. */

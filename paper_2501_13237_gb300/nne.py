@@ -209,6 +209,7 @@ class Context:
         nl, no = vals.shape
         lf = None if log_fid is None else np.ascontiguousarray(log_fid, dtype=np.float64)
         yz = None if y_zero is None else np.ascontiguousarray(y_zero, dtype=np.float64)
+        _check_fit_shapes(lam, lf, yz, nl, no)
         out = np.zeros(no)
         st = np.zeros(no, np.int32)
         _check(load().nne_extrapolate(self.h, nl, _hptr(lam), _hptr(vals), _hptr(lf), no, method, degree,
@@ -246,6 +247,7 @@ class Context:
         nl, no = vals.shape
         lf = None if log_fid is None else np.ascontiguousarray(log_fid, dtype=np.float64)
         yz = None if y_zero is None else np.ascontiguousarray(y_zero, dtype=np.float64)
+        _check_fit_shapes(lam, lf, yz, nl, no)
         out = np.zeros(no)
         st = np.zeros(no, np.int32)
         _check(load().nne_extrapolate_noalloc(self.h, nl, _hptr(lam), _hptr(vals), _hptr(lf), no, method, degree,
@@ -265,6 +267,17 @@ class Context:
                                     A.shape[0]))
 
 
+def _check_fit_shapes(lam, lf, yz, nl: int, no: int):
+    """The C side reads n_lambda levels and log-fidelities and n_obs lambda = 0
+    values from these host arrays: shorter arrays would be read past their end."""
+    if lam.shape != (nl,):
+        raise ValueError(f"lambdas has shape {lam.shape}, expected ({nl},)")
+    if lf is not None and lf.shape != (nl,):
+        raise ValueError(f"log_fid has shape {lf.shape}, expected ({nl},)")
+    if yz is not None and yz.shape != (no,):
+        raise ValueError(f"y_zero has shape {yz.shape}, expected ({no},)")
+
+
 def _vp(t):
     return C.c_void_p(_dptr(t))
 
@@ -276,6 +289,7 @@ def set_option(option: int, value: int):
 OPT_TENSOR_CORES = 0
 OPT_SUBBATCHES = 1
 OPT_SERIAL_LAYERS = 2
+OPT_EIG_FP64 = 3
 
 
 class State:
