@@ -66,6 +66,17 @@ PAULI_VEC = {
 }
 
 
+def svd(X: np.ndarray, compute_uv: bool = True):
+    """Thin SVD by LAPACK: the divide-and-conquer driver (gesdd), or, when it
+    reports non-convergence (it does on rare inputs), the QR-iteration driver
+    (gesvd).  Both compute the same decomposition."""
+    try:
+        return np.linalg.svd(X, full_matrices=False, compute_uv=compute_uv)
+    except np.linalg.LinAlgError:
+        import scipy.linalg
+        return scipy.linalg.svd(X, full_matrices=False, compute_uv=compute_uv, lapack_driver="gesvd")
+
+
 def fix_columns(W: np.ndarray) -> np.ndarray:
     """Gauge convention for an isometry: each column times conj(sum)/|sum| so that
     its column sum is real and non-negative (unchanged when the sum is zero)."""
@@ -152,7 +163,7 @@ class VMPO:
             A = self.M[k]
             cl, _, cr = A.shape
             Am = A.reshape(cl * 4, cr)
-            U, S, Vh = np.linalg.svd(Am, full_matrices=False)
+            U, S, Vh = svd(Am)
             r = min(chi_new, S.size)
             total = float(np.sum(S ** 2))
             kept = float(np.sum(S[:r] ** 2))
@@ -214,7 +225,7 @@ class VMPO:
         out = np.zeros(self.n - 1)
         for k in range(self.n - 1):
             A = self.M[k]
-            s = np.linalg.svd(A.reshape(A.shape[0] * 4, A.shape[2]), compute_uv=False)
+            s = svd(A.reshape(A.shape[0] * 4, A.shape[2]), compute_uv=False)
             out[k] = entropy_of_schmidt(s)
             self.move_centre(k + 1)
         return out
@@ -250,14 +261,14 @@ def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direc
     r = min(chi, 4 * cl, 4 * cr)
     if (direction > 0 and r == 4 * cl) or (direction < 0 and r == 4 * cr):
         # nothing can be cut on the isometry's side: keep the identity basis
-        S = np.linalg.svd(X, compute_uv=False)
+        S = svd(X, compute_uv=False)
         nrm = float(np.linalg.norm(X))
         if direction > 0:
             return np.eye(4 * cl, dtype=X.dtype).reshape(cl, 4, r), (X / nrm).reshape(r, 4, cr), 1.0, nrm, S
         return (X / nrm).reshape(cl, 4, r), np.eye(4 * cr, dtype=X.dtype).reshape(r, 4, cr), 1.0, nrm, S
     if r == min(4 * cl, 4 * cr):
         # nothing is cut, but the isometry's side is the larger one: exact QR split
-        S = np.linalg.svd(X, compute_uv=False)
+        S = svd(X, compute_uv=False)
         if direction > 0:
             Q, Rm = qr_fixed(X)
             nrm = float(np.linalg.norm(Rm))
@@ -265,7 +276,7 @@ def two_site_update(A: np.ndarray, B: np.ndarray, G: np.ndarray, chi: int, direc
         Q, Rm = qr_fixed(X.conj().T)
         nrm = float(np.linalg.norm(Rm))
         return (Rm.conj().T / nrm).reshape(cl, 4, r), Q.conj().T.reshape(r, 4, cr), 1.0, nrm, S
-    U, S, Vh = np.linalg.svd(X, full_matrices=False)
+    U, S, Vh = svd(X)
     total = float(np.sum(S ** 2))
     kept = float(np.sum(S[:r] ** 2))
     if direction > 0:
