@@ -4,10 +4,28 @@
 //   v_I = (1,0,0,1), v_X = (0,1,1,0), v_Y = (0,i,-i,0), v_Z = (1,0,0,-1).
 //   L_0 = 1, L_{k+1} = L_k T_I(k);  R_n = 1, R_k = T_I(k) R_{k+1};
 //   <P> = L_first T_P(first) ... T_P(last) R_{last+1} / L_n.
-// Accumulation in float64; each environment is rescaled to max-abs 1 and
-// its log-scale carried separately, so long chains neither overflow nor
-// underflow.
+//
+// Environment sweep (env_cluster_kernel): one thread-block cluster per
+// (pass, instance); the left pass and the right pass of every instance run at
+// the same time.  At each site the cluster's CTAs split the site tensor
+// (left pass: output columns b; right pass: rows a), stream it from HBM with
+// 16-byte coalesced loads, and exchange the new environment's slices and its
+// max-abs through distributed shared memory, one cluster barrier per site.
+// Besides the environments the sweep keeps, per site, the four partial
+// contractions
+//   ell_k[s][b] = sum_a L_k[a] M_k[a][s][b],   rho_k[t][a] = sum_b M_k[a][t][b] R_{k+1}[b],
+// so every Pauli string on one site or two neighbouring sites is a dot product
+// of stored vectors (obs_local_kernel) and the site tensors are read once per
+// pass.  Strings with a longer support take obs_kernel, which carries a vector
+// through the interior sites.
+// Accumulation: float64 for complex128 states; for complex64 states the
+// products are formed in float32, summed in float32 over at most 16 terms and
+// then added into float64 accumulators.  Each environment is rescaled to
+// max-abs 1 and its log-scale carried separately, so long chains neither
+// overflow nor underflow.
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace nne {
 
@@ -32,83 +50,305 @@ __device__ __forceinline__ T block_max(T v, T* red) {
   return t;
 }
 
-// Environment sweeps: blockIdx.x = 0 left, 1 right; one CTA per (pass, instance).
-// env layout: [inst][pass][k (0..n)][max_dim] complex double; scale [inst][pass][k].
-template <typename R>
-__global__ void __launch_bounds__(256) env_kernel(int n, const int* dims, const void* const* site,
-                                                   const long long* stride, int max_dim, double* env,
-                                                   double* envscale) {
-  __shared__ double red[32];
-  const int pass = blockIdx.x, z = blockIdx.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  cx<double>* E = reinterpret_cast<cx<double>*>(env) + ((long long)z * 2 + pass) * (n + 1) * max_dim;
-  double* ls = envscale + ((long long)z * 2 + pass) * (n + 1);
-  if (pass == 0) {
-    if (threadIdx.x == 0) { E[0] = mk<double>(1, 0); ls[0] = 0; }
-    __syncthreads();
-    for (int k = 0; k < n; ++k) {
-      const int dl = dims[k], dr = dims[k + 1];
-      const cx<R>* M = reinterpret_cast<const cx<R>*>(site[k]) + z * stride[k];
-      const cx<double>* Lk = E + (long long)k * max_dim;
-      cx<double>* Ln = E + (long long)(k + 1) * max_dim;
-      double mx = 0;
-      for (int b = threadIdx.x; b < dr; b += blockDim.x) {
-        cx<double> acc = mk<double>(0, 0);
-        for (int a = 0; a < dl; ++a) {
-          const cx<R> m0 = M[((long long)a * 4 + 0) * dr + b], m3 = M[((long long)a * 4 + 3) * dr + b];
-          fma_(acc, Lk[a], mk<double>((double)m0.re + m3.re, (double)m0.im + m3.im));
+namespace sweep {
+
+constexpr int THREADS = 256;
+constexpr int NB = 8;   // loads in flight per thread and batch; also the float32 run length before a float64 fold
+
+// Elements of one 16-byte load: two complex64 or one complex128.
+template <typename R> struct Vec;
+template <> struct Vec<float> { static constexpr int V = 2; };
+template <> struct Vec<double> { static constexpr int V = 1; };
+
+// Streaming loads (site tensors are read once per pass).
+template <typename R, int V>
+__device__ __forceinline__ void ldv(const cx<R>* p, cx<R>* o);
+template <>
+__device__ __forceinline__ void ldv<float, 2>(const cx<float>* p, cx<float>* o) {
+  const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+  o[0] = mk<float>(v.x, v.y);
+  o[1] = mk<float>(v.z, v.w);
+}
+template <>
+__device__ __forceinline__ void ldv<float, 1>(const cx<float>* p, cx<float>* o) {
+  const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+  o[0] = mk<float>(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ void ldv<double, 1>(const cx<double>* p, cx<double>* o) {
+  const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  o[0] = mk<double>(v.x, v.y);
+}
+
+__device__ __forceinline__ cx<double> up(cx<float> a) { return mk<double>(a.re, a.im); }
+__device__ __forceinline__ cx<double> up(cx<double> a) { return a; }
+
+// Shared-memory layout of env_cluster_kernel, in cx<double> units from the base.
+struct Layout {
+  int D, SL;
+  __host__ __device__ int cur() const { return 0; }                 // D: current environment (float64)
+  __host__ __device__ int slice() const { return D; }               // 2 x SL: this CTA's slice of the next one
+  __host__ __device__ int fin() const { return D + 2 * SL; }        // 4 x SL: left-pass results of this CTA
+  __host__ __device__ int part() const { return D + 6 * SL; }       // 2 x THREADS: row-group partial sums
+  __host__ __device__ int scal() const { return D + 6 * SL + 2 * THREADS; }   // 8 doubles (maxes, reduction)
+  __host__ __device__ int coef() const { return scal() + 8; }       // D x cx<R>: environment in the state's precision
+  __host__ __device__ size_t bytes(size_t esz) const { return 16 * (size_t)coef() + esz * (size_t)D; }
+};
+
+__host__ __device__ inline int slice_cap(int D, int cs) { return (D + cs - 1) / cs + 2; }
+
+__device__ __forceinline__ double block_max_sw(double v, double* red) {
+  for (int m = 16; m > 0; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0;
+  for (int i = 0; i < THREADS / 32; ++i) t = fmax(t, red[i]);
+  return t;
+}
+
+// Left pass at one site: fin[s][j] = sum_a coef[a] M[a][s][b0 + j] for this CTA's columns.
+template <typename R, int V>
+__device__ void left_site(const cx<R>* __restrict__ M, int dl, int dr, int b0, int w, const cx<R>* coef,
+                          cx<double>* fin, int SL, cx<double>* part) {
+  const int t = threadIdx.x;
+  const int wu = w / V, U = 4 * wu;
+  if (U == 0) return;
+  const int G = U >= THREADS ? 1 : THREADS / U;   // row groups
+  for (int u0 = 0; u0 < U; u0 += THREADS) {
+    const int u = u0 + (G > 1 ? t % U : t), g = G > 1 ? t / U : 0;
+    const bool act = u < U && g < G;
+    cx<double> acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = mk<double>(0, 0);
+    if (act) {
+      const int s = u / wu, j = (u % wu) * V;
+      const cx<R>* col = M + (long long)s * dr + b0 + j;
+      const long long rs = 4LL * dr * G;   // row step of this group
+      int a = g;
+      const cx<R>* p = col + (long long)a * 4 * dr;
+      while (a < dl) {
+        cx<R> m[NB][V];
+        cx<R> c[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          const int ai = a + i * G;
+          if (ai < dl) {
+            ldv<R, V>(p + i * rs, m[i]);
+            c[i] = coef[ai];
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) m[i][v] = mk<R>(0, 0);
+            c[i] = mk<R>(0, 0);
+          }
         }
-        Ln[b] = acc;
-        mx = fmax(mx, fmax(fabs(acc.re), fabs(acc.im)));
+        cx<R> s32[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) s32[v] = mk<R>(0, 0);
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+          for (int v = 0; v < V; ++v) fma_(s32[v], c[i], m[i][v]);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = acc[v] + up(s32[v]);
+        a += NB * G;
+        p += NB * rs;
       }
-      mx = block_max(mx, red);
-      const double inv = mx > 0 ? 1.0 / mx : 1.0;
-      for (int b = threadIdx.x; b < dr; b += blockDim.x) Ln[b] = inv * Ln[b];
-      if (threadIdx.x == 0) ls[k + 1] = ls[k] + (mx > 0 ? log(mx) : 0.0);
-      __syncthreads();
     }
-  } else {
-    if (threadIdx.x == 0) { E[(long long)n * max_dim] = mk<double>(1, 0); ls[n] = 0; }
-    __syncthreads();
-    for (int k = n - 1; k >= 0; --k) {
-      const int dl = dims[k], dr = dims[k + 1];
-      const cx<R>* M = reinterpret_cast<const cx<R>*>(site[k]) + z * stride[k];
-      const cx<double>* Rn = E + (long long)(k + 1) * max_dim;
-      cx<double>* Rk = E + (long long)k * max_dim;
-      double mx = 0;
-      for (int a = warp; a < dl; a += nw) {
-        cx<double> acc = mk<double>(0, 0);
-        for (int b = lane; b < dr; b += 32) {
-          const cx<R> m0 = M[((long long)a * 4 + 0) * dr + b], m3 = M[((long long)a * 4 + 3) * dr + b];
-          fma_(acc, mk<double>((double)m0.re + m3.re, (double)m0.im + m3.im), Rn[b]);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) {
-          Rk[a] = acc;
-          mx = fmax(mx, fmax(fabs(acc.re), fabs(acc.im)));
+    if (G == 1) {
+      if (act) {
+        const int s = u / wu, j = (u % wu) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) fin[s * SL + j + v] = acc[v];
+      }
+    } else {
+      // partial sums of the row groups, then added in group order
+      if (act)
+#pragma unroll
+        for (int v = 0; v < V; ++v) part[(g * U + u) * V + v] = acc[v];
+      __syncthreads();
+      if (t < U) {
+        const int s = t / wu, j = (t % wu) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          cx<double> tot = mk<double>(0, 0);
+          for (int gg = 0; gg < G; ++gg) tot = tot + part[(gg * U + t) * V + v];
+          fin[s * SL + j + v] = tot;
         }
       }
-      mx = block_max(mx, red);
-      const double inv = mx > 0 ? 1.0 / mx : 1.0;
-      for (int a = threadIdx.x; a < dl; a += blockDim.x) Rk[a] = inv * Rk[a];
-      if (threadIdx.x == 0) ls[k] = ls[k + 1] + (mx > 0 ? log(mx) : 0.0);
-      __syncthreads();
     }
   }
 }
 
-// One CTA per (observable, instance): carry S from R_{last+1} down to `first`.
+// Right pass at one site: rho[tt][a] = sum_b M[a][tt][b] coef[b] for this CTA's rows, one warp per row.
+// Writes rho to global memory and R[a] = rho[0][a] + rho[3][a] into the slice; returns the row max-abs.
+template <typename R, int V>
+__device__ double right_site(const cx<R>* __restrict__ M, int dr, int a0, int a1, const cx<R>* coef, cx<double>* rho,
+                             int D, cx<double>* slice) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = THREADS / 32;
+  const int nu = dr / V;   // units per segment
+  double mx = 0;
+  for (int a = a0 + warp; a < a1; a += nw) {
+    const cx<R>* row = M + (long long)a * 4 * dr;
+    cx<double> acc[4];
+#pragma unroll
+    for (int tt = 0; tt < 4; ++tt) {
+      acc[tt] = mk<double>(0, 0);
+      const cx<R>* seg = row + (long long)tt * dr;
+      for (int base = 0; base < nu; base += 32 * NB) {
+        cx<R> m[NB][V];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          const int uu = base + lane + 32 * i;
+          if (uu < nu) ldv<R, V>(seg + uu * V, m[i]);
+          else
+#pragma unroll
+            for (int v = 0; v < V; ++v) m[i][v] = mk<R>(0, 0);
+        }
+        cx<R> s32 = mk<R>(0, 0);
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          const int uu = base + lane + 32 * i;
+          if (uu < nu)
+#pragma unroll
+            for (int v = 0; v < V; ++v) fma_(s32, m[i][v], coef[uu * V + v]);
+        }
+        acc[tt] = acc[tt] + up(s32);
+      }
+      acc[tt] = warp_sum(acc[tt]);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int tt = 0; tt < 4; ++tt) rho[(long long)tt * D + a] = acc[tt];
+      const cx<double> Ra = acc[0] + acc[3];
+      slice[a - a0] = Ra;
+      mx = fmax(mx, fmax(fabs(Ra.re), fabs(Ra.im)));
+    }
+  }
+  return mx;
+}
+
+}  // namespace sweep
+
+// Both environment sweeps and the per-site partial contractions in one launch.
+// grid (cs, 2, n_inst), cluster (cs, 1, 1): cluster (pass, z); pass 0 left, 1 right.
+// env: [z][pass][k = 0..n][D] complex double, envscale: [z][pass][k], vecs: [z][pass][k = 0..n-1][4][D].
+template <typename R>
+__global__ void __launch_bounds__(sweep::THREADS) env_cluster_kernel(int n, const int* __restrict__ dims,
+                                                                    const void* const* __restrict__ site,
+                                                                    const long long* __restrict__ stride, int D,
+                                                                    double* env, double* envscale, double* vecs) {
+  using namespace sweep;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cs = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  const int pass = blockIdx.y, z = blockIdx.z, t = threadIdx.x;
+  constexpr int VV = Vec<R>::V;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Layout L{D, slice_cap(D, cs)};
+  cx<double>* base = reinterpret_cast<cx<double>*>(smem_raw);
+  cx<double>* cur = base + L.cur();
+  cx<double>* slice = base + L.slice();
+  cx<double>* fin = base + L.fin();
+  cx<double>* part = base + L.part();
+  double* scal = reinterpret_cast<double*>(base + L.scal());   // [0..1] maxes (double-buffered), [8..15] reduction
+  cx<R>* coef = reinterpret_cast<cx<R>*>(base + L.coef());
+  cx<double>* E = reinterpret_cast<cx<double>*>(env) + ((long long)z * 2 + pass) * (n + 1) * D;
+  double* ls = envscale + ((long long)z * 2 + pass) * (n + 1);
+  cx<double>* VK = reinterpret_cast<cx<double>*>(vecs) + ((long long)z * 2 + pass) * n * 4 * D;
+  const int first = pass == 0 ? 0 : n;
+  if (t == 0) {
+    cur[0] = mk<double>(1, 0);
+    coef[0] = mk<R>(1, 0);
+    if (rank == 0) {
+      E[(long long)first * D] = mk<double>(1, 0);
+      ls[first] = 0;
+    }
+  }
+  __syncthreads();
+  double lsc = 0;
+  int pb = 0;
+  for (int step = 0; step < n; ++step) {
+    const int k = pass == 0 ? step : n - 1 - step;
+    const int dl = dims[k], dr = dims[k + 1];
+    const cx<R>* M = reinterpret_cast<const cx<R>*>(site[k]) + z * stride[k];
+    const bool vec = VV > 1 && dr % VV == 0 && (reinterpret_cast<uintptr_t>(M) & 15) == 0;
+    cx<double>* sl = slice + pb * L.SL;
+    double mx = 0;
+    int own0, own1;   // entries of the next environment this CTA owns
+    if (pass == 0) {
+      const int v = vec ? VV : 1;
+      const int bs = ((dr + cs - 1) / cs + v - 1) / v * v;
+      const int b0 = min(dr, rank * bs), b1 = min(dr, b0 + bs);
+      own0 = b0;
+      own1 = b1;
+      if (vec) left_site<R, VV>(M, dl, dr, b0, b1 - b0, coef, fin, L.SL, part);
+      else left_site<R, 1>(M, dl, dr, b0, b1 - b0, coef, fin, L.SL, part);
+      __syncthreads();
+      cx<double>* ell = VK + (long long)k * 4 * D;
+      for (int q = t; q < 4 * (b1 - b0); q += THREADS) {
+        const int s = q / (b1 - b0), j = q % (b1 - b0);
+        ell[(long long)s * D + b0 + j] = fin[s * L.SL + j];
+      }
+      for (int j = t; j < b1 - b0; j += THREADS) {
+        const cx<double> Lb = fin[j] + fin[3 * L.SL + j];
+        sl[j] = Lb;
+        mx = fmax(mx, fmax(fabs(Lb.re), fabs(Lb.im)));
+      }
+    } else {
+      const int rs = (dl + cs - 1) / cs;
+      const int a0 = min(dl, rank * rs), a1 = min(dl, a0 + rs);
+      own0 = a0;
+      own1 = a1;
+      cx<double>* rho = VK + (long long)k * 4 * D;
+      mx = vec ? right_site<R, VV>(M, dr, a0, a1, coef, rho, D, sl) : right_site<R, 1>(M, dr, a0, a1, coef, rho, D, sl);
+    }
+    mx = block_max_sw(mx, scal + 8);
+    if (t == 0) scal[pb] = mx;
+    (void)own0;
+    (void)own1;
+    cluster.sync();   // every slice and max of this site is published
+    // the next environment, normalised to max-abs 1, gathered from the cluster's slices
+    double m = 0;
+    for (int r = 0; r < cs; ++r) m = fmax(m, *cluster.map_shared_rank(scal + pb, r));
+    const double inv = m > 0 ? 1.0 / m : 1.0;
+    const int nd = pass == 0 ? dr : dl;               // length of the next environment
+    int width;
+    if (pass == 0) {
+      const int v = vec ? VV : 1;
+      width = ((dr + cs - 1) / cs + v - 1) / v * v;
+    } else {
+      width = (dl + cs - 1) / cs;
+    }
+    const int knext = pass == 0 ? k + 1 : k;
+    for (int i = t; i < nd; i += THREADS) {
+      const int r = i / width;
+      const cx<double> val = cluster.map_shared_rank(slice + pb * L.SL, r)[i - r * width];
+      const cx<double> nv = inv * val;
+      cur[i] = nv;
+      coef[i] = mk<R>((R)nv.re, (R)nv.im);
+      if (rank == 0) E[(long long)knext * D + i] = nv;
+    }
+    lsc += m > 0 ? log(m) : 0.0;
+    if (rank == 0 && t == 0) ls[knext] = lsc;
+    pb ^= 1;
+    __syncthreads();
+  }
+  cluster.sync();   // no CTA leaves while a peer may still read its shared memory
+}
+
+// Strings whose support spans three or more sites: one CTA per (string,
+// instance) carries S from R_{last+1} down to `first`; idx lists the strings.
 template <typename R>
 __global__ void __launch_bounds__(256) obs_kernel(int n, const int* dims, const void* const* site,
                                                    const long long* stride, int max_dim, const double* env,
                                                    const double* envscale, const uint8_t* paulis, const int* first,
-                                                   const int* last, int n_obs, double* out) {
+                                                   const int* last, const int* idx, int n_obs, double* out) {
   extern __shared__ unsigned char smem_raw[];
   cx<double>* S = reinterpret_cast<cx<double>*>(smem_raw);
   cx<double>* S2 = S + max_dim;
   __shared__ double red[32];
   __shared__ cx<double> cred[32];
-  const int o = blockIdx.x, z = blockIdx.y;
+  const int o = idx[blockIdx.x], z = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const cx<double>* EL = reinterpret_cast<const cx<double>*>(env) + ((long long)z * 2 + 0) * (n + 1) * max_dim;
   const cx<double>* ER = reinterpret_cast<const cx<double>*>(env) + ((long long)z * 2 + 1) * (n + 1) * max_dim;
@@ -175,29 +415,134 @@ __global__ void __launch_bounds__(256) obs_kernel(int n, const int* dims, const 
   }
 }
 
+// Strings on at most two neighbouring sites (and the identity): one warp per
+// (string, instance), dot products of the stored per-site vectors:
+//   one site k:      sum_b (sum_s v_P[s] ell_k[s][b]) R_{k+1}[b]
+//   sites k, k + 1:  sum_c (sum_s v_P[s] ell_k[s][c]) (sum_t v_Q[t] rho_{k+1}[t][c])
+__global__ void __launch_bounds__(256) obs_local_kernel(int n, const int* __restrict__ dims, int D,
+                                                        const double* env, const double* envscale,
+                                                        const double* vecs, const uint8_t* __restrict__ paulis,
+                                                        const int* __restrict__ first, const int* __restrict__ last,
+                                                        int n_obs, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), z = blockIdx.y;
+  if (o >= n_obs) return;
+  const int f = first[o], l = last[o];
+  double* res = out + ((long long)z * n_obs + o) * 2;
+  if (f < 0) {
+    if (lane == 0) { res[0] = 1.0; res[1] = 0.0; }
+    return;
+  }
+  if (l - f > 1) return;
+  const cx<double>* EL = reinterpret_cast<const cx<double>*>(env) + ((long long)z * 2 + 0) * (n + 1) * D;
+  const cx<double>* ER = reinterpret_cast<const cx<double>*>(env) + ((long long)z * 2 + 1) * (n + 1) * D;
+  const double* lsL = envscale + ((long long)z * 2 + 0) * (n + 1);
+  const double* lsR = envscale + ((long long)z * 2 + 1) * (n + 1);
+  const cx<double>* ell = reinterpret_cast<const cx<double>*>(vecs) + (((long long)z * 2 + 0) * n + f) * 4 * D;
+  const int P = paulis[(long long)o * n + f];
+  const cx<double> p0 = pvec(P, 0), p1 = pvec(P, 1), p2 = pvec(P, 2), p3 = pvec(P, 3);
+  const int d = dims[f + 1];
+  cx<double> acc = mk<double>(0, 0);
+  double lscale;
+  if (l == f) {
+    const cx<double>* Rn = ER + (long long)(f + 1) * D;
+    for (int b = lane; b < d; b += 32) {
+      cx<double> u = mk<double>(0, 0);
+      fma_(u, p0, ell[b]);
+      fma_(u, p1, ell[D + b]);
+      fma_(u, p2, ell[2 * D + b]);
+      fma_(u, p3, ell[3 * D + b]);
+      fma_(acc, u, Rn[b]);
+    }
+    lscale = lsL[f] + lsR[f + 1];
+  } else {
+    const cx<double>* rho = reinterpret_cast<const cx<double>*>(vecs) + (((long long)z * 2 + 1) * n + l) * 4 * D;
+    const int Q = paulis[(long long)o * n + l];
+    const cx<double> q0 = pvec(Q, 0), q1 = pvec(Q, 1), q2 = pvec(Q, 2), q3 = pvec(Q, 3);
+    for (int c = lane; c < d; c += 32) {
+      cx<double> u = mk<double>(0, 0), w = mk<double>(0, 0);
+      fma_(u, p0, ell[c]);
+      fma_(u, p1, ell[D + c]);
+      fma_(u, p2, ell[2 * D + c]);
+      fma_(u, p3, ell[3 * D + c]);
+      fma_(w, q0, rho[c]);
+      fma_(w, q1, rho[D + c]);
+      fma_(w, q2, rho[2 * D + c]);
+      fma_(w, q3, rho[3 * D + c]);
+      fma_(acc, u, w);
+    }
+    lscale = lsL[f] + lsR[l + 1];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const cx<double> tr = EL[(long long)n * D];
+    const double scale = exp(lscale - lsL[n]);
+    const double den = tr.re * tr.re + tr.im * tr.im;
+    const double qr = (acc.re * tr.re + acc.im * tr.im) / den, qi = (acc.im * tr.re - acc.re * tr.im) / den;
+    res[0] = qr * scale;
+    res[1] = qi * scale;
+  }
+}
+
+// Cluster size of the environment sweep: two clusters (left, right pass) per
+// instance; 16 CTAs per cluster while that keeps the grid within the GPU,
+// else 8; small bonds take fewer.
+static int sweep_cluster_size(int n_inst, int D) {
+  if (D < 16) return 1;
+  if (D < 64) return 4;
+  return 2 * n_inst * 16 <= 128 ? 16 : 8;
+}
+
 template <typename R>
 cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* const* d_site,
                          const long long* d_stride, int n_inst, int max_dim, int n_obs, const uint8_t* d_paulis,
-                         const int* d_first, const int* d_last, double* d_env, double* d_envscale, double* d_out) {
+                         const int* d_first, const int* d_last, const int* d_general, int n_general, double* d_env,
+                         double* d_envscale, double* d_vecs, double* d_out) {
   cudaError_t e;
   {
+    const int cs = sweep_cluster_size(n_inst, max_dim);
+    const sweep::Layout L{max_dim, sweep::slice_cap(max_dim, cs)};
+    const size_t smem = L.bytes(sizeof(cx<R>));
+    if ((e = ensure_kernel_smem((const void*)env_cluster_kernel<R>, smem, cs > 8)) != cudaSuccess) return e;
+    // algorithmic bytes: every site tensor read once by each pass
     ProfScope ps(st, K_SWEEP_ENV);
-    env_kernel<R><<<dim3(2, n_inst), 256, 0, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale);
-    e = cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 2, n_inst);
+    cfg.blockDim = dim3(sweep::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, env_cluster_kernel<R>, n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale,
+                           d_vecs);
   }
   if (e != cudaSuccess) return e;
   if (n_obs <= 0) return cudaSuccess;
+  {
+    ProfScope ps(st, K_SWEEP_OBS);
+    obs_local_kernel<<<dim3((n_obs + 7) / 8, n_inst), 256, 0, st>>>(n, d_dims, max_dim, d_env, d_envscale, d_vecs,
+                                                                   d_paulis, d_first, d_last, n_obs, d_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (n_general <= 0) return cudaSuccess;
   const size_t smem = 2 * sizeof(cx<double>) * (size_t)max_dim;
   if ((e = ensure_kernel_smem((const void*)obs_kernel<R>, smem, false)) != cudaSuccess) return e;
   ProfScope ps(st, K_SWEEP_OBS);
-  obs_kernel<R><<<dim3(n_obs, n_inst), 256, smem, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale,
-                                                        d_paulis, d_first, d_last, n_obs, d_out);
+  obs_kernel<R><<<dim3(n_general, n_inst), 256, smem, st>>>(n, d_dims, d_site, d_stride, max_dim, d_env, d_envscale,
+                                                            d_paulis, d_first, d_last, d_general, n_obs, d_out);
   return cudaGetLastError();
 }
 
-template cudaError_t expect_sweep<float>(cudaStream_t, int, const int*, const void* const*, const long long*, int, int,
-                                         int, const uint8_t*, const int*, const int*, double*, double*, double*);
-template cudaError_t expect_sweep<double>(cudaStream_t, int, const int*, const void* const*, const long long*, int,
-                                          int, int, const uint8_t*, const int*, const int*, double*, double*, double*);
+#define NNE_INST_SWEEP(R)                                                                                          \
+  template cudaError_t expect_sweep<R>(cudaStream_t, int, const int*, const void* const*, const long long*, int, int, \
+                                       int, const uint8_t*, const int*, const int*, const int*, int, double*, double*, \
+                                       double*, double*);
+NNE_INST_SWEEP(float)
+NNE_INST_SWEEP(double)
 
 }  // namespace nne
