@@ -394,8 +394,12 @@ __global__ void __launch_bounds__(256, 1) cgemm_tc_kernel(int M, int N, int K, f
 static int g_tc_enabled = 1;
 static __device__ int g_tc_error = 0;
 
+static int g_tma_enabled = 1;
+
 void set_tensor_cores(int on) { g_tc_enabled = on ? 1 : 0; }
 int tensor_cores_enabled() { return g_tc_enabled; }
+void set_gemm_tma(int on) { g_tma_enabled = on ? 1 : 0; }
+int gemm_tma_enabled() { return g_tma_enabled; }
 
 // Device address of the tensor-core kernels' error word (per device, looked up once).
 int* tc_error_ptr() {
@@ -439,6 +443,14 @@ __global__ void __launch_bounds__(256) cgemm_split_reduce_kernel(int M, int N, i
     }
     *c = v;
   }
+}
+
+cudaError_t cgemm_split_reduce(cudaStream_t st, int M, int N, int S, const float2* P, float2 alpha, float2 beta,
+                               float2* C, long long sC, int ldc, int batch) {
+  const long long mn = (long long)M * N;
+  const int blocks = (int)std::min<long long>((mn + 255) / 256, 2048);
+  cgemm_split_reduce_kernel<<<dim3(blocks, batch), 256, 0, st>>>(M, N, S, P, alpha, beta, C, sC, ldc);
+  return cudaGetLastError();
 }
 
 template <int OPA, int OPB>
