@@ -5,10 +5,11 @@ Workload: n = 100 qubits, 1D brickwork of Haar-random U(4) gates (seed 0),
 every gate followed by two-qubit depolarizing p = 5e-4*lambda, amplitude
 damping gamma = 1e-3*lambda and dephasing 5e-4*lambda on both qubits, 8 noise
 levels lambda = 1..8 run as 8 instances of one state, chi = 512, complex64
-with the randomized range finder truncation (k = chi + 64, one power
-iteration), observables all <Z_i> and <X_i X_i+1>, weighted log-linear
-extrapolation (exponential fallback) to lambda* = 1.  Synthetic inputs from
-workloads/ (no datasets).
+(split-TF32 tensor-core GEMMs), the SVD truncation of Sec. 2.1.2 reached by
+subspace iteration (k = 640 columns, 4 power iterations, Rayleigh-Ritz),
+observables all <Z_i> and
+<X_i X_i+1>, weighted log-linear extrapolation (exponential fallback) to
+lambda* = 1.  Synthetic inputs from workloads/ (no datasets).
 
 One step = two brickwork layers of the saturated regime (99 gates x 8
 instances = 792 two-qubit gate+truncation steps, every bond at chi = 512)
@@ -26,6 +27,12 @@ roofline   the dominant kernel class from live CUDA-event timing of one more
            headline steps are timed without them) and its layers on one
            stream (NNE_OPT_SERIAL_LAYERS), so that each launch is timed alone;
            achieved = algorithmic flops per launch / average launch time.
+fp64_path  the plain float64 path on the same GPU: one instance (lambda = 1),
+           complex128, exact truncation (Gram matrix + float64 eigensolve),
+           gate steps timed one call each from the saturated state.
+accuracy   <P> of the fast path against the complex128 exact-SVD path after
+           the same prefix of gates from the same saturated state.
+measured_peaks  TF32 and FP64 torch.matmul rates of this GPU (roofline peaks).
 cpu_baseline / --impl reference: the CPU oracle (NumPy, float64) timed on a
            bounded sample: full-size gate steps at chi = 512 on the host cores.
 serving    an open-loop Poisson request stream through nne_submit / nne_poll
@@ -55,10 +62,13 @@ sys.path.insert(0, ROOT)
 import numpy as np
 
 CHI = 512
-OVERSAMPLE = 64
-POWER_ITERS = 1
+SUBSPACE_COLS = 640          # k: columns of the subspace iteration (chi + 128)
+POWER_ITERS = 4              # q: power iterations, each re-orthonormalised
 LAYERS_PER_STEP = 2
 SATURATE_LAYERS = 6          # bond dims 4, 16, 64, 256, 512 reached by layer 5
+FP64_GATES = 4               # gate steps timed on the plain complex128 single-instance path
+CHECK_GATES = 16             # prefix on which <P> of the fast path is compared with complex128 exact
+CHECK_LEVELS = (0, 7)        # noise levels (lambda = 1 and 8) of that comparison
 
 
 def peaks():
@@ -164,6 +174,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=20.0, help="offered requests per second")
     ap.add_argument("--batch", type=int, default=64,
                     help="circuits of the 64-circuit batch workload added to the line (0: none)")
+    ap.add_argument("--no-checks", action="store_true",
+                    help="skip the float64 arm, the <P> check, the peak and CPU measurements (profiling runs)")
     ap.add_argument("--subbatches", type=int, default=None,
                     help="concurrent sub-batches per state (NNE_OPT_SUBBATCHES; library default when omitted)")
     args = ap.parse_args()
@@ -193,7 +205,7 @@ def main():
     if args.subbatches is not None:
         nne.set_option(nne.OPT_SUBBATCHES, args.subbatches)
     st = nne.State(ctx, w.n, CHI, n_inst, nne.C64, nne.TRUNC_RSVD, w.bits())
-    st.set_sketch(wl.gaussian_sketch(4 * CHI, CHI + OVERSAMPLE, 1234).astype(np.complex64), POWER_ITERS)
+    st.set_sketch(wl.gaussian_sketch(4 * CHI, SUBSPACE_COLS, 1234).astype(np.complex64), POWER_ITERS)
 
     dev = f"cuda:{local}"
     U_dev = [torch.from_numpy(np.ascontiguousarray(us)).to(dev) for _, us, _ in plan]
@@ -208,6 +220,8 @@ def main():
         qs, _, d = plan[li]
         st.apply_layer(qs, ctx.build_superops(U_dev[li], rates_dev, out=G_buf[li]), d)
     st.sync()
+    # the saturated state of two levels, for the complex128 comparison after the timed steps
+    snap = snapshot(st, CHECK_LEVELS) if rank == 0 and not args.no_checks else None
     cursor = [SATURATE_LAYERS]
 
     def next_layers():
@@ -294,9 +308,17 @@ def main():
     dominant = max(prof.items(), key=lambda kv: kv[1][0])
     prof_summary = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in prof.items() if v[1]}
     prof_summary["_step_ms"] = round(ms_prof, 3)
-    roof = roofline(dominant, prof, pk)
+    roof = None
+    fast_lat = gate_latencies(st, ctx, plan, cursor[0], rates_dev, 6)
     cpu = None
-    if rank == 0:
+    fp64 = check = pk_meas = None
+    if rank == 0 and not args.no_checks:
+        st.close()
+        torch.cuda.empty_cache()
+        fp64 = fp64_path(ctx, w, plan, snap, rates)
+        check = prefix_check(ctx, w, plan, snap, rates, paulis)
+        pk_meas = measure_peaks(dev)
+        roof = roofline(dominant, prof, pk, pk_meas)
         n_cpu = 3
         dt = cpu_oracle_steps(n_cpu)
         cpu = {"value": n_cpu / dt, "unit": "gate_steps/s", "cores": threads_used(), "kind": "oracle",
@@ -305,7 +327,8 @@ def main():
         for k, (t, c, wk) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
             if c:
                 sys.stderr.write(f"  {k:18s} {t:10.2f} ms  {c:7d} launches  {100 * t / max(ms_prof, 1e-9):5.1f}%\n")
-    st.close()
+    if rank != 0 or args.no_checks:
+        st.close()
     serving = None
     if rank == 0 and args.serving > 0:
         serving = serving_run(args.serving, args.serving_rate, 0, 4, local)
@@ -318,13 +341,19 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
                 "data": "synthetic",
                 "config": {"workload": "n100_d30_chi512_8lambda", "chi": CHI, "n": w.n, "n_lambda": n_inst,
-                           "truncation": f"randomized range finder k=chi+{OVERSAMPLE}, q={POWER_ITERS}",
+                           "truncation": (f"SVD truncation to chi (Sec. 2.1.2) by subspace iteration: k={SUBSPACE_COLS} "
+                                          f"columns, q={POWER_ITERS} power iterations, Rayleigh-Ritz (float32 eigensolve; "
+                                          "the float64 eigensolve variant in accuracy.fp64_eigensolve); complex64, "
+                                          "3xTF32 tensor-core GEMMs; <P> checked against the complex128 exact-SVD "
+                                          "path (accuracy)"),
                            "step": f"{LAYERS_PER_STEP} saturated brickwork layers ({gates_per_step} gate steps) "
                                    "+ 199-observable sweep + fit",
                            "l2": "inputs larger than L2 (state ~6.7 GB)", "parallelism": f"replicas{world}"},
                 "e2e": {"value": e2e, "unit": "gate_steps/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "fp64_path": fp64, "fast_gate_latency_ms": fast_lat, "accuracy": check,
+                "measured_peaks": pk_meas,
                 "kernel_classes_ms": prof_summary, "serving": serving, "batch": batch}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -333,40 +362,191 @@ def main():
 
 # FP32 SIMT peak of GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2070 MHz max SM clock.
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
-# TF32 dense tensor peak: measured bf16 x nominal TF32/bf16 ratio (1.1 / 2.25).
-TF32_RATIO = 1.1 / 2.25
 ALU_CLASSES = {"gemm": "float32 SIMT GEMMs", "wy_apply": "split-K block-reflector products",
                "qr_factor": "Householder panel factorisation", "tridiag": "Hermitian tridiagonalisation"}
 
 
-def roofline(dominant, prof, pk):
+def roofline(dominant, prof, pk, meas):
     """Roofline entry of the dominant kernel class, from live CUDA-event timing.
 
     achieved = the algorithmic real flops the library records per launch of the
     class (8 per complex multiply-add; 16/3 n^3 per tridiagonalisation) summed
     over the timed region / the class's summed launch time.  Tensor-core GEMMs
-    (complex64 as three TF32 products per real product) take the TF32 peak,
-    derived from the measured bf16 peak with the nominal TF32/bf16 ratio; the
-    others run on the FP32 pipes and take the derived FP32 SIMT peak."""
+    (complex64 as three TF32 products per real product) take the TF32 peak
+    measured in this run with torch.matmul, sustained (the class is timed inside
+    a seconds-long step); the others run on the FP32 pipes and take the derived
+    FP32 SIMT peak."""
     name, (t_ms, count, work) = dominant
     if count == 0 or t_ms <= 0:
         return None
     out = {"kernel": name, "launches": count, "avg_launch_ms": t_ms / count, "traffic": None}
     achieved = work / (t_ms / 1e3) / 1e12 if work > 0 else None
     if name == "gemm_tc" and achieved is not None:
-        # timed inside a seconds-long step: the sustained bf16 figure
-        peak = pk["bf16_tflops_sustained"] * TF32_RATIO
+        peak = meas["tf32_tflops_sustained"]
         out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "peak_source": f"{pk['source']} sustained bf16 {pk['bf16_tflops_sustained']} x 1.1/2.25 (TF32); "
-                                   "complex64 runs as 3 TF32 products per real product, so at most 1/3 of it "
-                                   "is algorithmic"})
+                    "peak_source": "measured in this run: torch.matmul float32 with TF32, 8192^3, back to back "
+                                   "for 2 s (sustained); complex64 runs as 3 TF32 products per real product, so "
+                                   "at most 1/3 of it is algorithmic"})
     elif name in ALU_CLASSES and achieved is not None:
         out.update({"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "what": ALU_CLASSES[name],
                     "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"})
     else:
         out.update({"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None})
+    return out
+
+
+def snapshot(st, levels):
+    """Host copy of the given levels of a state: sites, centre, log-norm, log F."""
+    dims, centre, ln, lf = st.info()
+    return {"levels": list(levels), "centre": centre, "ln": ln[list(levels)], "lf": lf[list(levels)],
+            "sites": [[st.read_site(i, k) for k in range(st.n)] for i in levels]}
+
+
+def restore(ctx, nne, w, snap, which, dtype, trunc, k=None, q=None):
+    """A new state of the snapshot's levels `which` (indices into snap['levels'])."""
+    s = nne.State(ctx, w.n, CHI, len(which), dtype, trunc, w.bits())
+    if trunc == nne.TRUNC_RSVD:
+        import workloads as wl
+        om = wl.gaussian_sketch(4 * CHI, k, 1234)
+        s.set_sketch(om.astype(np.complex64 if dtype == nne.C64 else np.complex128), q)
+    for j, i in enumerate(which):
+        for kk, M in enumerate(snap["sites"][i]):
+            s.write_site(j, kk, M)
+    s.set_centre(snap["centre"])
+    s.set_log(snap["ln"][list(which)], snap["lf"][list(which)])
+    s.sync()
+    return s
+
+
+def gate_latencies(st, ctx, plan, li, rates_dev, n_gates):
+    """Per-gate-step latency (ms) of the fast path: the first gates of layer li,
+    one nne_apply_layer call each, CUDA events on the library's stream."""
+    import torch
+    qs, us, d = plan[li]
+    U = torch.from_numpy(np.ascontiguousarray(us[:n_gates])).to(rates_dev.device)
+    G = ctx.build_superops(U, rates_dev)
+    Gg = [G[:, g:g + 1].contiguous() for g in range(n_gates)]
+    ms = []
+    for g in range(n_gates):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        st.apply_layer([qs[g]], Gg[g], d)
+        e1.record(ctx.stream)
+        st.sync()
+        ms.append(e0.elapsed_time(e1))
+    return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)), "gates": n_gates,
+            "n_inst": int(rates_dev.shape[0]), "what": "one gate step of all levels, complex64 fast path"}
+
+
+def fp64_path(ctx, w, plan, snap, rates):
+    """The plain float64 path on one instance (lambda = 1): complex128 state,
+    exact truncation (Gram matrix and float64 eigensolve), the first gates of
+    the layer after the saturated ones, one call per gate, CUDA events."""
+    import torch
+    from paper_2501_13237_gb300 import nne
+    s = restore(ctx, nne, w, snap, [0], nne.C128, nne.TRUNC_EXACT)
+    qs, us, d = plan[SATURATE_LAYERS]
+    G = ctx.build_superops(np.ascontiguousarray(us[:FP64_GATES + 1]), np.ascontiguousarray(rates[:1]))
+    Gg = [G[:, g:g + 1].contiguous() for g in range(FP64_GATES + 1)]
+    s.apply_layer([qs[0]], Gg[0], d)       # warm-up
+    s.sync()
+    ms = []
+    for g in range(1, FP64_GATES + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        s.apply_layer([qs[g]], Gg[g], d)
+        e1.record(ctx.stream)
+        s.sync()
+        ms.append(e0.elapsed_time(e1))
+    s.close()
+    torch.cuda.empty_cache()
+    return {"value": 1e3 * len(ms) / sum(ms), "unit": "gate_steps/s", "dtype": "c128", "n_inst": 1,
+            "truncation": "exact: Gram matrix + float64 Householder/bisection/inverse iteration",
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)), "gates": len(ms)}
+
+
+def prefix_check(ctx, w, plan, snap, rates, paulis):
+    """<P> error of the fast path: from the same saturated state, the first
+    CHECK_GATES gates of the next layer on the fast complex64 path and on the
+    complex128 exact-SVD path, then every observable on both."""
+    import torch
+    from paper_2501_13237_gb300 import nne
+    qs, us, d = plan[SATURATE_LAYERS]
+    lev = list(snap["levels"])
+    G = ctx.build_superops(np.ascontiguousarray(us[:CHECK_GATES]), np.ascontiguousarray(rates[lev]))
+    out, secs = {}, {}
+    for name, dt, tr, k, q, e in (("c128", nne.C128, nne.TRUNC_EXACT, None, None, 0),
+                                  ("fast", nne.C64, nne.TRUNC_RSVD, SUBSPACE_COLS, POWER_ITERS, 0),
+                                  ("fast_fp64_eig", nne.C64, nne.TRUNC_RSVD, SUBSPACE_COLS, POWER_ITERS, 1)):
+        nne.set_option(nne.OPT_EIG_FP64, e)
+        s = restore(ctx, nne, w, snap, list(range(len(lev))), dt, tr, k, q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.apply_layer(qs[:CHECK_GATES], G, d)
+        s.sync()
+        secs[name] = time.perf_counter() - t0
+        out[name] = s.expect(paulis)
+        s.close()
+        nne.set_option(nne.OPT_EIG_FP64, 0)
+        torch.cuda.empty_cache()
+    err = np.abs(out["fast"][0].real - out["c128"][0].real)
+    err64 = np.abs(out["fast_fp64_eig"][0].real - out["c128"][0].real)
+    steps = CHECK_GATES * len(lev)
+    return {"max_abs_err_P": float(err.max()), "mean_abs_err_P": float(err.mean()),
+            "dlogF": (out["fast"][1] - out["c128"][1]).tolist(), "prefix_gates": CHECK_GATES,
+            "levels_lambda": [float(w.lambdas[i]) for i in lev], "n_obs": int(paulis.shape[0]),
+            "vs": "complex128 exact-SVD path on the GPU, same saturated state",
+            "fp64_eigensolve": {"max_abs_err_P": float(err64.max()),
+                                "dlogF": (out["fast_fp64_eig"][1] - out["c128"][1]).tolist(),
+                                "gate_steps_per_s_prefix": steps / secs["fast_fp64_eig"],
+                                "what": "the same fast path with the Rayleigh-Ritz eigensolve's reduction, "
+                                        "bisection and inverse iteration in float64 (NNE_OPT_EIG_FP64)"},
+            "gate_steps_per_s_prefix": {k2: steps / v for k2, v in secs.items()}}
+
+
+def measure_peaks(dev):
+    """Dense TF32 and FP64 matmul rates of this GPU (torch.matmul, cuBLAS):
+    TF32 8192^3 best of 10 (burst) and back to back for 2 s (sustained), FP64
+    4096^3 best of 3."""
+    import torch
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dt, n, reps, tf32 in (("tf32", torch.float32, 8192, 10, True), ("fp64", torch.float64, 4096, 3, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device=dev, dtype=dt)
+            b = torch.randn(n, n, device=dev, dtype=dt)
+            c = a @ b
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                c = a @ b
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            out[f"{name}_tflops"] = 2 * n ** 3 / best / 1e12
+            if name == "tf32":
+                t0 = time.perf_counter()
+                cnt = 0
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                while time.perf_counter() - t0 < 2.0:
+                    c = a @ b
+                    cnt += 1
+                    if cnt % 8 == 0:
+                        torch.cuda.synchronize()
+                e1.record()
+                torch.cuda.synchronize()
+                out["tf32_tflops_sustained"] = cnt * 2 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = "torch.matmul: float32 with TF32 8192^3 (best of 10; back to back 2 s), float64 4096^3 best of 3"
     return out
 
 

@@ -270,17 +270,29 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
  * NNE_OPT_SERIAL_LAYERS (default 0): when 1, nne_apply_layer runs all of a
  * state's instances as one batch on the context stream, whatever the state's
  * sub-batch count -- for per-launch timing of the kernels alone.
- * NNE_OPT_EIG_FP64 (default 1): complex64 states solve the truncation's
- * Hermitian eigenproblems (the Gram matrix of the exact truncation, the
- * Rayleigh-Ritz matrix of the subspace iteration, the centre compression)
- * with the Householder reduction, bisection and inverse iteration in float64
- * and the back-transformation in float32; 0 runs all of it in float32 (for
- * comparisons).  complex128 states always use float64.
+ * NNE_OPT_EIG_FP64 (default 0): when 1, complex64 states solve the
+ * truncation's Hermitian eigenproblems (the Gram matrix of the exact
+ * truncation, the Rayleigh-Ritz matrix of the subspace iteration, the centre
+ * compression) with the Householder reduction, bisection and inverse
+ * iteration in float64 and the back-transformation in float32; 0 runs them
+ * in float32.  complex128 states always use float64.
+ * NNE_OPT_GEMM_TMA (default 1): large complex64 GEMMs (M >= 128, N >= 64,
+ * K >= 64) split their operands once into TF32 planes and run the TMA-fed
+ * tcgen05 kernel; 0 keeps the earlier tensor-core kernel that splits inside
+ * its producer warps (for comparisons).
+ * NNE_OPT_TEST_WAIT_LIMIT (test hook, default 0): bound, in polls, of the
+ * TMA GEMM's pipeline mbarrier waits; 0 is the default bound, a negative
+ * value makes every such wait expire at once.  An expired wait makes the
+ * kernel record NNE_ERR_TIMEOUT (reported once by the next nne_sync or
+ * nne_cgemm_c64, then cleared) and return after waiting, with the full
+ * bound, for its own copies and MMAs.
  * Options are process-wide; set them while no other thread calls the library. */
 #define NNE_OPT_TENSOR_CORES 0
 #define NNE_OPT_SUBBATCHES 1
 #define NNE_OPT_SERIAL_LAYERS 2
 #define NNE_OPT_EIG_FP64 3
+#define NNE_OPT_GEMM_TMA 4
+#define NNE_OPT_TEST_WAIT_LIMIT 5
 void nne_set_option(int option, int value);
 
 /* Wait for the state's enqueued work; returns the first device-side error. */

@@ -81,6 +81,11 @@ cudaError_t cgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<R> 
                   long long sA, int lda, const cx<R>* B, long long sB, int ldb, cx<R> beta, cx<R>* C,
                   long long sC, int ldc, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return cudaSuccess;
+  if (std::is_same<R, float>::value && tensor_cores_enabled() && gemm_tma_enabled() && M >= 128 && N >= 64 &&
+      K >= 64 && cgemm_tma_available())
+    return cgemm_tma(st, opA, opB, M, N, K, *reinterpret_cast<const cx<float>*>(&alpha),
+                     reinterpret_cast<const cx<float>*>(A), sA, lda, reinterpret_cast<const cx<float>*>(B), sB, ldb,
+                     *reinterpret_cast<const cx<float>*>(&beta), reinterpret_cast<cx<float>*>(C), sC, ldc, batch);
   if (std::is_same<R, float>::value && tensor_cores_enabled() && M >= 64 && N >= 64 && K >= 64)
     return cgemm_tc(st, opA, opB, M, N, K, *reinterpret_cast<const cx<float>*>(&alpha),
                     reinterpret_cast<const cx<float>*>(A), sA, lda, reinterpret_cast<const cx<float>*>(B), sB, ldb,
@@ -174,18 +179,22 @@ cudaError_t sumsq_partial(cudaStream_t st, const cx<R>* X, long long sX, long lo
 
 // Gate bookkeeping per instance: kept = sum of kept parts, total = sum of total
 // parts; scale[z] = 1/sqrt(kept); log_norm += log sqrt(kept); log_fid += log(kept/total).
-__global__ void finish_gate_kernel(const double* kept_parts, const double* total_parts, int parts, int batch,
-                                   double* scale, double* log_norm, double* log_fid, int* err) {
+// kept = ||C||^2 normalises the kept factor C; f = kept / total, or, when the
+// discarded weight ||X - P X||^2 is given, f = (total - discarded) / total.
+__global__ void finish_gate_kernel(const double* kept_parts, const double* total_parts, const double* disc_parts,
+                                   int parts, int batch, double* scale, double* log_norm, double* log_fid, int* err) {
   const int z = blockIdx.x * blockDim.x + threadIdx.x;
   if (z >= batch) return;
-  double kept = 0, total = 0;
+  double kept = 0, total = 0, disc = 0;
   for (int p = 0; p < parts; ++p) kept += kept_parts[z * parts + p];
   if (total_parts) {
     for (int p = 0; p < parts; ++p) total += total_parts[z * parts + p];
   } else {
     total = kept;
   }
-  if (!(kept > 0) || !(total > 0) || !isfinite(kept) || !isfinite(total)) {
+  if (disc_parts)
+    for (int p = 0; p < parts; ++p) disc += disc_parts[z * parts + p];
+  if (!(kept > 0) || !(total > 0) || !isfinite(kept) || !isfinite(total) || !isfinite(disc)) {
     atomicExch(err, NNE_ERR_NOCONV);
     scale[z] = 1.0;
     return;
@@ -193,8 +202,12 @@ __global__ void finish_gate_kernel(const double* kept_parts, const double* total
   const double nrm = sqrt(kept);
   scale[z] = 1.0 / nrm;
   log_norm[z] += log(nrm);
-  double f = kept / total;
+  double f = disc_parts ? (total - disc) / total : kept / total;
   if (f > 1.0) f = 1.0;
+  if (!(f > 0)) {
+    atomicExch(err, NNE_ERR_NOCONV);
+    return;
+  }
   log_fid[z] += log(f);
 }
 
@@ -307,6 +320,26 @@ cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y
   return cudaGetLastError();
 }
 
+template <typename R>
+__global__ void copy2d_kernel(const cx<R>* X, long long sX, int ldx, cx<R>* Y, long long sY, int ldy, int rows,
+                              int cols) {
+  X += blockIdx.y * sX;
+  Y += blockIdx.y * sY;
+  const long long count = (long long)rows * cols;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    Y[(i / cols) * ldy + i % cols] = X[(i / cols) * ldx + i % cols];
+}
+
+template <typename R>
+cudaError_t copy_2d(cudaStream_t st, const cx<R>* X, long long sX, int ldx, cx<R>* Y, long long sY, int ldy, int rows,
+                    int cols, int batch) {
+  if (rows <= 0 || cols <= 0 || batch <= 0) return cudaSuccess;
+  ProfScope ps(st, K_ELEMWISE);
+  const int blocks = (int)std::min<long long>(((long long)rows * cols + 255) / 256, 1024);
+  copy2d_kernel<R><<<dim3(blocks, batch), 256, 0, st>>>(X, sX, ldx, Y, sY, ldy, rows, cols);
+  return cudaGetLastError();
+}
+
 // Gauge fixing of an isometry W (n x r, ld r): column j is multiplied by
 // conj(sum_i W[i][j]) / |sum_i W[i][j]| so that its column sum is real and
 // non-negative (a zero sum leaves the column unchanged).
@@ -395,6 +428,7 @@ cudaError_t product_state(cudaStream_t st, int n, void* const* d_site, const lon
   template cudaError_t conj_inplace<R>(cudaStream_t, cx<R>*, long long, long long, int);                         \
   template cudaError_t identity<R>(cudaStream_t, cx<R>*, long long, int, int, int);                              \
   template cudaError_t copy_batched<R>(cudaStream_t, const cx<R>*, long long, cx<R>*, long long, long long, int); \
+  template cudaError_t copy_2d<R>(cudaStream_t, const cx<R>*, long long, int, cx<R>*, long long, int, int, int, int); \
   template cudaError_t product_state<R>(cudaStream_t, int, void* const*, const long long*, int, const uint8_t*); \
   template cudaError_t fix_columns<R>(cudaStream_t, cx<R>*, long long, int, int, int);                          \
   template cudaError_t fix_qr<R>(cudaStream_t, cx<R>*, long long, int, int, cx<R>*, long long, int, int);
@@ -402,11 +436,11 @@ cudaError_t product_state(cudaStream_t st, int n, void* const* d_site, const lon
 NNE_INST_BLAS(float)
 NNE_INST_BLAS(double)
 
-cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, int parts, int batch,
-                        double* scale, double* log_norm, double* log_fid, int* err) {
+cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, const double* disc_parts,
+                        int parts, int batch, double* scale, double* log_norm, double* log_fid, int* err) {
   ProfScope ps(st, K_ELEMWISE);
-  finish_gate_kernel<<<(batch + 127) / 128, 128, 0, st>>>(kept_parts, total_parts, parts, batch, scale, log_norm,
-                                                          log_fid, err);
+  finish_gate_kernel<<<(batch + 127) / 128, 128, 0, st>>>(kept_parts, total_parts, disc_parts, parts, batch, scale,
+                                                          log_norm, log_fid, err);
   return cudaGetLastError();
 }
 

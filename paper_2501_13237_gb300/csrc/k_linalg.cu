@@ -487,6 +487,166 @@ cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R
   return qr<R>(st, U, sU, n, r, U, sU, nullptr, 0, qrws, batch);
 }
 
+// ---------------------------------------------------------------- mixed precision
+// Top r eigenvalues (descending) of the real tridiagonal (d, e) in float64,
+// one thread each: bisection on Sturm counts from the Gershgorin interval to
+// a bracket of width 4 eps ||T||.  (The warp multisection above takes 32
+// Sturm counts per step; in float64, whose rate on GB300 is 1/64 of float32,
+// one count per step is the cheaper schedule.)
+__global__ void __launch_bounds__(128) bisect64_kernel(const double* db, const double* eb, int n, int r, int ldde,
+                                                       double* lamb, int ldl, int total) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= total) return;
+  const int z = gid / r, t = gid % r;
+  const double* d = db + (long long)z * ldde;
+  const double* e = eb + (long long)z * ldde;
+  double lo = 1e300, hi = -1e300, emax = 0;
+  for (int k = 0; k < n; ++k) {
+    const double rad = (k > 0 ? e[k - 1] : 0.0) + (k + 1 < n ? e[k] : 0.0);
+    lo = fmin(lo, d[k] - rad);
+    hi = fmax(hi, d[k] + rad);
+    if (k + 1 < n) emax = fmax(emax, e[k]);
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = DBL_MIN * fmax(1.0, emax * emax);
+  lo -= 4 * DBL_EPSILON * tnorm + pivmin;
+  hi += 4 * DBL_EPSILON * tnorm + pivmin;
+  const int idx = n - 1 - t;
+  const double tol = 4 * DBL_EPSILON * tnorm + 2 * pivmin;
+  for (int it = 0; it < 128 && (hi - lo) > tol; ++it) {
+    const double x = 0.5 * (lo + hi);
+    if (sturm_count(d, e, n, x, pivmin) <= idx) lo = x;
+    else hi = x;
+  }
+  lamb[(long long)z * ldl + t] = 0.5 * (lo + hi);
+}
+
+__global__ void cx_f2d_kernel(const cx<float>* X, long long sX, int rows, int cols, int ldx, cx<double>* Y,
+                              long long sY) {
+  const long long count = (long long)rows * cols;
+  const int z = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const cx<float> v = X[z * sX + (i / cols) * ldx + i % cols];
+    Y[z * sY + i] = mk<double>(v.re, v.im);
+  }
+}
+
+__global__ void cx_d2f_kernel(const cx<double>* X, cx<float>* Y, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    Y[i] = mk<float>((float)X[i].re, (float)X[i].im);
+}
+
+__global__ void re_d2f_kernel(const double* X, float* Y, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    Y[i] = (float)X[i];
+}
+
+static inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+MixedEighWork eigh_mixed_workspace(int n, int r) {
+  // per matrix; every array is batch-major, so a batch of b matrices needs b times these bytes
+  MixedEighWork w;
+  const size_t nn = (size_t)n * n, nr = (size_t)n * r;
+  const int nbw = (n + 31) / 32;
+  w.cx_bytes = al256(16 * nn) * 2 + al256(16 * (size_t)n) * 3 + al256(8 * nn) + al256(8 * (size_t)n) +
+               al256(8 * (size_t)nbw * 1024) + al256(8 * (size_t)wy_workspace(r)) +
+               al256(8 * (size_t)qr_workspace(n, r).cx_elems) + 1024;
+  w.re_bytes = al256(8 * (size_t)n) * 2 + al256(8 * (size_t)r) + al256(8 * nr) * 5 + al256(4 * nr) + 512 + 1024;
+  w.u8_bytes = al256(nr) + 256;
+  return w;
+}
+
+// Top-r eigenvectors of the complex64 Hermitian H[z] (n x n, ld n), written to
+// U[z] (n x r, ld r, columns by decreasing eigenvalue, orthonormal).  The
+// Householder reduction, the eigenvalues (bisection) and the eigenvectors of
+// the tridiagonal (inverse iteration) run in float64; the back-transformation
+// through the reflectors and the final orthonormalisation run in float32.  A
+// float32 reduction has a backward error of eps_32 ||H||, which turns the
+// eigenvectors next to the truncation cut by eps_32 ||H|| / gap there (about
+// 0.1 on saturated chi = 512 states); in float64 that error is below the
+// rounding of the input, and the float32 back-transformation only adds
+// eps_32-sized, gap-independent errors.
+cudaError_t eigh_top_mixed(cudaStream_t st, cx<float>* H, long long sH, int n, int r, cx<float>* U, long long sU,
+                           void* cx_ws, void* re_ws, void* u8_ws, int batch, int* err) {
+  (void)err;
+  if (batch <= 0) return cudaSuccess;
+  const size_t nn = (size_t)n * n, nr = (size_t)n * r;
+  const int nbw = (n + 31) / 32;
+  const size_t B = (size_t)batch;
+  unsigned char* c = reinterpret_cast<unsigned char*>(cx_ws);
+  auto take = [&](unsigned char*& base, size_t bytes) {
+    unsigned char* p = base;
+    base += al256(bytes);
+    return p;
+  };
+  cx<double>* Hd = reinterpret_cast<cx<double>*>(take(c, 16 * nn * B));
+  cx<double>* Vhd = reinterpret_cast<cx<double>*>(take(c, 16 * nn * B));
+  cx<double>* ed = reinterpret_cast<cx<double>*>(take(c, 16 * (size_t)n * B));
+  cx<double>* phid = reinterpret_cast<cx<double>*>(take(c, 16 * (size_t)n * B));
+  cx<double>* Pd = reinterpret_cast<cx<double>*>(take(c, 16 * (size_t)n * B));
+  cx<float>* Vhf = reinterpret_cast<cx<float>*>(take(c, 8 * nn * B));
+  cx<float>* phif = reinterpret_cast<cx<float>*>(take(c, 8 * (size_t)n * B));
+  cx<float>* Tw = reinterpret_cast<cx<float>*>(take(c, 8 * (size_t)nbw * 1024 * B));
+  cx<float>* wyws = reinterpret_cast<cx<float>*>(take(c, 8 * (size_t)wy_workspace(r) * B));
+  cx<float>* qrws = reinterpret_cast<cx<float>*>(take(c, 8 * (size_t)qr_workspace(n, r).cx_elems * B));
+  unsigned char* q = reinterpret_cast<unsigned char*>(re_ws);
+  double* dd = reinterpret_cast<double*>(take(q, 8 * (size_t)n * B));
+  double* eabs = reinterpret_cast<double*>(take(q, 8 * (size_t)n * B));
+  double* lam = reinterpret_cast<double*>(take(q, 8 * (size_t)r * B));
+  double* Z = reinterpret_cast<double*>(take(q, 8 * nr * B));
+  double* Ls = reinterpret_cast<double*>(take(q, 8 * nr * B));
+  double* U0 = reinterpret_cast<double*>(take(q, 8 * nr * B));
+  double* U1 = reinterpret_cast<double*>(take(q, 8 * nr * B));
+  double* U2 = reinterpret_cast<double*>(take(q, 8 * nr * B));
+  float* Zf = reinterpret_cast<float*>(take(q, 4 * nr * B));
+  double* Kp = reinterpret_cast<double*>(take(q, 8 * 32 * B));
+  uint8_t* piv = reinterpret_cast<uint8_t*>(u8_ws);
+  cudaError_t ce;
+  {
+    ProfScope ps(st, K_ELEMWISE);
+    cx_f2d_kernel<<<dim3((unsigned)std::min<size_t>((nn + 255) / 256, 1024), batch), 256, 0, st>>>(H, sH, n, n, n, Hd,
+                                                                                                (long long)nn);
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  if ((ce = cudaMemsetAsync(Vhd, 0, 16 * nn * B, st)) != cudaSuccess) return ce;
+  if (smem_cluster_size<double>(n) > 0) {
+    ce = tridiag_smem<double>(st, Hd, (long long)nn, n, dd, ed, n, Vhd, (long long)nn, batch);
+  } else {
+    const int cs = cluster_size_for(n);
+    ProfScope ps(st, K_TRIDIAG, 1, 16.0 / 3.0 * (double)n * n * n * batch);
+    ce = launch_cluster(tridiag_kernel<double>, cs, batch, 2 * sizeof(cx<double>) * (size_t)n, st, Hd, (long long)nn,
+                        n, dd, ed, n, Pd, Kp, Vhd, (long long)nn);
+  }
+  if (ce != cudaSuccess) return ce;
+  {
+    ProfScope ps(st, K_ELEMWISE);
+    tridiag_phases_kernel<double><<<batch, 256, 0, st>>>(ed, n, n, eabs, phid);
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  const int total = batch * r;
+  {
+    ProfScope ps(st, K_BISECT);
+    bisect64_kernel<<<(total + 127) / 128, 128, 0, st>>>(dd, eabs, n, r, n, lam, r, total);
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  {
+    ProfScope ps(st, K_INVITER);
+    inviter_kernel<double><<<(total + 127) / 128, 128, 0, st>>>(dd, eabs, n, r, n, lam, r, Z, (long long)nr, Ls, U0,
+                                                                U1, U2, piv, (long long)nr, total);
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  {
+    ProfScope ps(st, K_ELEMWISE);
+    cx_d2f_kernel<<<1024, 256, 0, st>>>(Vhd, Vhf, (long long)(nn * B));
+    cx_d2f_kernel<<<64, 256, 0, st>>>(phid, phif, (long long)(n * B));
+    re_d2f_kernel<<<1024, 256, 0, st>>>(Z, Zf, (long long)(nr * B));
+  }
+  if ((ce = cudaGetLastError()) != cudaSuccess) return ce;
+  ce = backtransform_wy<float>(st, Vhf, (long long)nn, n, Zf, (long long)nr, phif, n, r, U, sU, Tw, wyws, batch);
+  if (ce != cudaSuccess) return ce;
+  return qr<float>(st, U, sU, n, r, U, sU, nullptr, 0, qrws, batch);
+}
+
 template <typename R>
 cudaError_t gram_entropy(cudaStream_t st, cx<R>* H, long long sH, int n, void* cx_ws, void* re_ws, int batch,
                          double* S, long long sS) {

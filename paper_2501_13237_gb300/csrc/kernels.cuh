@@ -17,8 +17,8 @@ cudaError_t apply_superop(cudaStream_t st, cx<R>* X, long long sX, int dl, int d
 template <typename R>
 cudaError_t sumsq_partial(cudaStream_t st, const cx<R>* X, long long sX, long long count, double* out, int parts,
                           int batch);
-cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, int parts, int batch,
-                        double* scale, double* log_norm, double* log_fid, int* err);
+cudaError_t finish_gate(cudaStream_t st, const double* kept_parts, const double* total_parts, const double* disc_parts,
+                        int parts, int batch, double* scale, double* log_norm, double* log_fid, int* err);
 template <typename R>
 cudaError_t scale_batched(cudaStream_t st, cx<R>* X, long long sX, long long count, const double* scale, int batch);
 template <typename R>
@@ -31,6 +31,11 @@ cudaError_t identity(cudaStream_t st, cx<R>* X, long long sX, int rows, int cols
 template <typename R>
 cudaError_t copy_batched(cudaStream_t st, const cx<R>* X, long long sX, cx<R>* Y, long long sY, long long count,
                          int batch);
+
+// Y[z] (rows x cols, ld ldy) = X[z] (rows x cols, ld ldx).
+template <typename R>
+cudaError_t copy_2d(cudaStream_t st, const cx<R>* X, long long sX, int ldx, cx<R>* Y, long long sY, int ldy, int rows,
+                    int cols, int batch);
 
 template <typename R>
 cudaError_t product_state(cudaStream_t st, int n, void* const* d_site, const long long* d_stride, int n_inst,
@@ -48,6 +53,23 @@ cudaError_t cgemm_tc(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<
 void set_tensor_cores(int on);
 int tensor_cores_enabled();
 int* tc_error_ptr();
+// C[z] = alpha sum_s P[z S + s] + beta C[z] over the S K-slices of a split GEMM (M x N each, ld N).
+cudaError_t cgemm_split_reduce(cudaStream_t st, int M, int N, int S, const float2* P, float2 alpha, float2 beta,
+                               float2* C, long long sC, int ldc, int batch);
+// ---- k_gemm_tma.cu (complex64 on tcgen05, operands pre-split into TF32 planes and fed by TMA)
+cudaError_t cgemm_tma(cudaStream_t st, int opA, int opB, int M, int N, int K, cx<float> alpha, const cx<float>* A,
+                      long long sA, int lda, const cx<float>* B, long long sB, int ldb, cx<float> beta, cx<float>* C,
+                      long long sC, int ldc, int batch);
+bool cgemm_tma_available();
+// Split op(A) (M x K) into TF32 planes now and let this host thread's later
+// cgemm_tma calls on `st` with exactly this A, op, shape and batch reuse them
+// (A must not change until tma_release(st), which frees the planes).
+cudaError_t tma_hold_a(cudaStream_t st, int opA, int M, int K, const cx<float>* A, long long sA, int lda, int batch);
+void tma_release(cudaStream_t st);
+// Test hook: bound (polls) of the TMA GEMM's pipeline waits; 0 restores the default.
+void set_tc_wait_limit(long long polls);
+void set_gemm_tma(int on);
+int gemm_tma_enabled();
 
 // ---- k_linalg.cu
 // Workspace sizes (elements) for eigh_top on n x n matrices with r wanted vectors.
@@ -63,6 +85,16 @@ EighWork eigh_workspace(int n, int r);
 template <typename R>
 cudaError_t eigh_top(cudaStream_t st, cx<R>* H, long long sH, int n, int r, cx<R>* U, long long sU, void* cx_ws,
                      void* re_ws, void* u8_ws, int batch, int* err);
+
+// Bytes per matrix of eigh_top_mixed's three workspaces.
+struct MixedEighWork {
+  size_t cx_bytes, re_bytes, u8_bytes;
+};
+MixedEighWork eigh_mixed_workspace(int n, int r);
+// Top-r eigenvectors of complex64 Hermitian matrices with the reduction and the
+// tridiagonal eigenproblem in float64 (see k_linalg.cu); same layout as eigh_top.
+cudaError_t eigh_top_mixed(cudaStream_t st, cx<float>* H, long long sH, int n, int r, cx<float>* U, long long sU,
+                           void* cx_ws, void* re_ws, void* u8_ws, int batch, int* err);
 
 // Entropy -sum p ln p of the normalised eigenvalues p of each Hermitian
 // positive semi-definite H[z] (n x n, overwritten), written to S[z * sS]:
@@ -110,11 +142,14 @@ struct SweepSites {
   const void* const* site;   // per site k: pointer to instance 0's tensor
   const long long* stride;   // per site k: elements between instances
 };
+// d_env: n_inst x 2 x (n + 1) x max_dim complex double; d_envscale: n_inst x 2 x (n + 1);
+// d_vecs: n_inst x 2 x n x 4 x max_dim complex double; d_general lists the n_general
+// strings whose support spans three or more sites.
 template <typename R>
 cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* const* d_site,
                          const long long* d_stride, int n_inst, int max_dim, int n_obs, const uint8_t* d_paulis,
-                         const int* d_first, const int* d_last, double* d_env, double* d_envscale,
-                         double* d_out /* n_inst x n_obs x 2 */);
+                         const int* d_first, const int* d_last, const int* d_general, int n_general, double* d_env,
+                         double* d_envscale, double* d_vecs, double* d_out /* n_inst x n_obs x 2 */);
 
 // ---- k_superop.cu
 cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int n_inst, const double* d_rates,

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -123,6 +124,25 @@ std::vector<int> bond_caps(int n, int chi) {
 
 static size_t round256(size_t b) { return ((b == 0 ? 16 : b) + 255) & ~size_t(255); }
 
+// Eigensolver workspace per instance in elements of the state's precision
+// (complex, real, bytes): the float path's needs, and for complex64 states
+// also those of the mixed-precision path (float64 arrays carved from the same
+// blocks), each rounded to 256 bytes so every instance's block stays aligned.
+EighWork eigh_workspace_state(int n, int r, int dtype) {
+  EighWork w = eigh_workspace(n, r);
+  if (dtype == NNE_C64) {
+    const MixedEighWork m = eigh_mixed_workspace(n, r);
+    w.cx_elems = std::max<long long>(w.cx_elems, (long long)((m.cx_bytes + 4096 + 7) / 8));
+    w.re_elems = std::max<long long>(w.re_elems, (long long)((m.re_bytes + 4096 + 3) / 4));
+    w.u8_elems = std::max<long long>(w.u8_elems, (long long)(m.u8_bytes + 256));
+  }
+  const long long cq = 256 / (dtype == NNE_C64 ? 8 : 16), rq = 256 / (dtype == NNE_C64 ? 4 : 8);
+  w.cx_elems = (w.cx_elems + cq - 1) / cq * cq;
+  w.re_elems = (w.re_elems + rq - 1) / rq * rq;
+  w.u8_elems = (w.u8_elems + 255) / 256 * 256;
+  return w;
+}
+
 // Device bytes nne_create_state (and nne_set_sketch, when sketch_cols > 0)
 // allocate for these arguments: the same blocks, rounded the same way.
 size_t state_bytes(int n, int chi, int n_inst, int dtype, int sketch_rows, int sketch_cols) {
@@ -137,12 +157,12 @@ size_t state_bytes(int n, int chi, int n_inst, int dtype, int sketch_rows, int s
     arena = (arena + 255) & ~size_t(255);
   }
   total += round256(arena);
-  total += round256(sizeof(double) * (3 * (size_t)n_inst + 2 * (size_t)n_inst * PARTS) + 64);
+  total += round256(sizeof(double) * (3 * (size_t)n_inst + 3 * (size_t)n_inst * PARTS) + 64);
   const long long D = dmax, N4 = 4 * D;
   total += round256((size_t)(N4 * N4) * n_inst * esz) * 3;     // X, H, T
   total += round256((size_t)(N4 * D) * n_inst * esz);          // U
   total += round256((size_t)std::max(N4 * D, D * D) * n_inst * esz);
-  const EighWork ew = eigh_workspace((int)N4, (int)D);
+  const EighWork ew = eigh_workspace_state((int)N4, (int)D, dtype);
   total += round256((size_t)ew.cx_elems * n_inst * esz);
   total += round256((size_t)ew.re_elems * n_inst * (esz / 2) + 256);
   total += round256((size_t)ew.u8_elems * n_inst);
@@ -216,6 +236,8 @@ int g_substreams = 4;
 // When set, nne_apply_layer runs every state's instances as one batch on the
 // context stream (nne_set_option NNE_OPT_SERIAL_LAYERS).
 int g_serial_layers = 0;
+// complex64 eigenproblems with a float64 reduction and tridiagonal solve (NNE_OPT_EIG_FP64).
+int g_eig_fp64 = 0;
 
 void destroy_streams(nne_state* s) {
   for (cudaStream_t q : s->sub_st) cudaStreamDestroy(q);
@@ -273,16 +295,43 @@ inline uint8_t* eigu8(nne_state* s, const BatchView& b) {
   return reinterpret_cast<uint8_t*>(s->eig_u8) + (long long)b.i0 * s->eig_u8_pi;
 }
 
-// Norm bookkeeping after a split: kept = ||C||^2, total = ||X||^2 (or kept).
+// The projection P X of a truncating split as a product of its two factors
+// (rows x cols = op(F) op(G), K = r): X <- X - P X gives the discarded part.
 template <typename R>
-nne_status finish_split(nne_state* s, const BatchView& b, cx<R>* C, long long sC, long long countC, const cx<R>* Xt, long long sXt,
-                        long long countX) {
+struct SplitProduct {
+  int opF, opG, M, N, K;
+  const cx<R>* F;
+  long long sF;
+  int ldf;
+  const cx<R>* G;
+  long long sG;
+  int ldg;
+};
+
+// Norm bookkeeping after a split: kept = ||C||^2 normalises C, total =
+// ||X||^2 (or kept), f = kept / total.  For complex64 truncations the kept
+// weight of f is taken as total - ||X - P X||^2 instead: the tensor cores'
+// float32 accumulation truncates, which biases ||C||^2 = ||W^H X||^2 low by
+// about 1e-5 relative at K = 2048 -- as large as a tenth of a typical gate's
+// discarded weight -- while the residual's own bias is relative to the small
+// discarded part.  X is overwritten by the residual.
+template <typename R>
+nne_status finish_split(nne_state* s, const BatchView& b, cx<R>* C, long long sC, long long countC, cx<R>* Xt,
+                        long long sXt, long long countX, const SplitProduct<R>* px = nullptr) {
   cudaStream_t st = b.st;
   double* kept = s->d_parts + (long long)b.i0 * PARTS;
   double* total = s->d_parts + (long long)s->n_inst * PARTS + (long long)b.i0 * PARTS;
+  double* disc = s->d_parts + 2LL * s->n_inst * PARTS + (long long)b.i0 * PARTS;
   CTRY(sumsq_partial<R>(st, C, sC, countC, kept, PARTS, b.nb));
   if (Xt) CTRY(sumsq_partial<R>(st, Xt, sXt, countX, total, PARTS, b.nb));
-  CTRY(finish_gate(st, kept, Xt ? total : nullptr, PARTS, b.nb, s->d_scale + b.i0, s->d_lognorm + b.i0, s->d_logfid + b.i0, s->d_err));
+  const bool resid = Xt && px && std::is_same<R, float>::value;
+  if (resid) {
+    CTRY(cgemm<R>(st, px->opF, px->opG, px->M, px->N, px->K, mk<R>(-1, 0), px->F, px->sF, px->ldf, px->G, px->sG,
+                  px->ldg, mk<R>(1, 0), Xt, sXt, px->N, b.nb));
+    CTRY(sumsq_partial<R>(st, Xt, sXt, countX, disc, PARTS, b.nb));
+  }
+  CTRY(finish_gate(st, kept, Xt ? total : nullptr, resid ? disc : nullptr, PARTS, b.nb, s->d_scale + b.i0,
+                   s->d_lognorm + b.i0, s->d_logfid + b.i0, s->d_err));
   CTRY(scale_batched<R>(st, C, sC, countC, s->d_scale + b.i0, b.nb));
   return NNE_OK;
 }
@@ -350,13 +399,29 @@ nne_status move_centre(nne_state* s, const std::vector<BatchView>& views, int ta
   return NNE_OK;
 }
 
+// Top-r eigenvectors of the Hermitian H (n x n) into W (n x r): complex64
+// states take the float64 reduction and tridiagonal solve unless disabled.
+template <typename R>
+nne_status eigh_state(nne_state* s, const BatchView& b, cx<R>* H, long long sH, int n, int r, cx<R>* W, long long sW) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (g_eig_fp64)
+      return check<R>(eigh_top_mixed(b.st, H, sH, n, r, W, sW, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb,
+                                     s->d_err),
+                      "eigh_top_mixed");
+  }
+  return check<R>(eigh_top<R>(b.st, H, sH, n, r, W, sW, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err),
+                  "eigh_top");
+}
+
 // Top-r left (dir > 0) or right (dir < 0) singular subspace of X[z] as an
 // isometry W (n_side x r, ld r) in s->U.
 //  exact: eigenvectors of the Gram matrix X X^H (or X^H X);
-//  randomized (Halko-Martinsson-Tropp): Y = X Omega (k columns), q power
-//    iterations Y <- X X^H Q each followed by re-orthonormalisation, Rayleigh-Ritz on
-//    C = (Q^H X)(Q^H X)^H, W = Q * (top-r eigenvectors of C).  Used when
-//    k < n_side; otherwise the sketch spans the space and the exact path runs.
+//  subspace iteration (Halko-Martinsson-Tropp): Y = X Omega (k columns), q
+//    power iterations Y <- X X^H Q each followed by re-orthonormalisation,
+//    Rayleigh-Ritz on C = (Q^H X)(Q^H X)^H, W = Q * (top-r eigenvectors of C).
+//    With enough columns and iterations it reaches the SVD truncation's
+//    subspace (the kept weight converges from below); used when k < n_side,
+//    otherwise the sketch spans the space and the exact path runs.
 template <typename R>
 nne_status subspace(nne_state* s, const BatchView& b, cx<R>* X, int rows, int cols, int r, int dir) {
   cudaStream_t st = b.st;
@@ -366,7 +431,8 @@ nne_status subspace(nne_state* s, const BatchView& b, cx<R>* X, int rows, int co
   const int n = dir > 0 ? rows : cols;
   const int other = dir > 0 ? cols : rows;
   const int k = s->omega_cols;
-  if (s->trunc == NNE_TRUNC_RSVD && s->d_omega && k < n && k >= r) {
+  const bool rsvd = s->trunc == NNE_TRUNC_RSVD && s->d_omega && k < n && k >= r;
+  if (rsvd) {
     cx<R>* Om = reinterpret_cast<cx<R>*>(s->d_omega);
     cx<R>* Y = wsb<R>(s->rs_Y, s->rs_sY, b);    // n x k
     cx<R>* Z = wsb<R>(s->rs_Z, s->rs_sZ, b);    // other x k
@@ -375,6 +441,16 @@ nne_status subspace(nne_state* s, const BatchView& b, cx<R>* X, int rows, int co
     const long long sY = s->rs_sY, sZ = s->rs_sZ, sC = s->rs_sC, sW = s->rs_sW;
     // A = X (dir > 0) or X^H (dir < 0): A is n x other
     const int opA = dir > 0 ? OP_N : OP_C, opAh = dir > 0 ? OP_C : OP_N;
+    // X feeds 2 q + 2 products in both forms: split it into TF32 planes once each
+    const bool hold = std::is_same<R, float>::value && tensor_cores_enabled() && gemm_tma_enabled() &&
+                      cgemm_tma_available() && n >= 128 && other >= 128 && k >= 64;
+    if constexpr (std::is_same<R, float>::value) {
+      tma_release(st);   // nothing held from an earlier step that ended in an error
+      if (hold) {
+        CTRY(tma_hold_a(st, opA, n, other, X, s->sX, cols, b.nb));
+        CTRY(tma_hold_a(st, opAh, other, n, X, s->sX, cols, b.nb));
+      }
+    }
     CTRY(cgemm<R>(st, opA, OP_N, n, k, other, one, X, s->sX, cols, Om, 0, k, zero, Y, sY, k, b.nb));
     CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, qrws<R>(s, b), b.nb));
     // power iterations Y <- A (A^H Q), re-orthonormalised after each application of A A^H
@@ -384,25 +460,26 @@ nne_status subspace(nne_state* s, const BatchView& b, cx<R>* X, int rows, int co
       CTRY(qr<R>(st, Y, sY, n, k, Y, sY, nullptr, 0, qrws<R>(s, b), b.nb));
     }
     if (k == r) {   // the sketch space itself is the answer
+      if (hold) tma_release(st);
       CTRY(copy_batched<R>(st, Y, sY, W, s->sU, (long long)n * k, b.nb));
       CTRY(fix_columns<R>(st, W, s->sU, n, r, b.nb));
       return NNE_OK;
     }
     // Bt = A^H Q (other x k); C = Bt^H Bt (k x k)
     CTRY(cgemm<R>(st, opAh, OP_N, other, k, n, one, X, s->sX, cols, Y, sY, k, zero, Z, sZ, k, b.nb));
+    if (hold) tma_release(st);
     CTRY(cgemm<R>(st, OP_C, OP_N, k, k, other, one, Z, sZ, k, Z, sZ, k, zero, Cm, sC, k, b.nb));
-    CTRY(eigh_top<R>(st, Cm, sC, k, r, Wk, sW, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err));
+    TRY(eigh_state<R>(s, b, Cm, sC, k, r, Wk, sW));
     CTRY(cgemm<R>(st, OP_N, OP_N, n, r, k, one, Y, sY, k, Wk, sW, r, zero, W, s->sU, r, b.nb));
-    CTRY(fix_columns<R>(st, W, s->sU, n, r, b.nb));
-    return NNE_OK;
+  } else {
+    if (dir > 0)
+      CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, cols, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, rows,
+                    b.nb));
+    else
+      CTRY(cgemm<R>(st, OP_C, OP_N, cols, cols, rows, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, cols,
+                    b.nb));
+    TRY(eigh_state<R>(s, b, Hm, s->sH, n, r, W, s->sU));
   }
-  if (dir > 0)
-    CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, cols, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, rows,
-                  b.nb));
-  else
-    CTRY(cgemm<R>(st, OP_C, OP_N, cols, cols, rows, one, X, s->sX, cols, X, s->sX, cols, zero, Hm, s->sH, cols,
-                  b.nb));
-  CTRY(eigh_top<R>(st, Hm, s->sH, n, r, W, s->sU, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err));
   CTRY(fix_columns<R>(st, W, s->sU, n, r, b.nb));
   return NNE_OK;
 }
@@ -440,7 +517,8 @@ nne_status gate_compute(nne_state* s, const BatchView& b, int q, const double* G
       CTRY(copy_batched<R>(st, W, s->sU, A, s->sstride[q], (long long)rows * r, b.nb));
       CTRY(cgemm<R>(st, OP_C, OP_N, r, cols, rows, mk<R>(1, 0), W, s->sU, r, X, s->sX, cols, mk<R>(0, 0), B,
                     s->sstride[q + 1], cols, b.nb));
-      TRY(finish_split<R>(s, b, B, s->sstride[q + 1], (long long)r * cols, X, s->sX, countX));
+      const SplitProduct<R> px{OP_N, OP_N, rows, cols, r, W, s->sU, r, B, s->sstride[q + 1], cols};   // W B'
+      TRY(finish_split<R>(s, b, B, s->sstride[q + 1], (long long)r * cols, X, s->sX, countX, &px));
     }
   } else {
     if (r == cols) {
@@ -464,7 +542,8 @@ nne_status gate_compute(nne_state* s, const BatchView& b, int q, const double* G
       CTRY(transpose<R>(st, true, W, s->sU, cols, r, r, B, s->sstride[q + 1], cols, b.nb));
       CTRY(cgemm<R>(st, OP_N, OP_N, rows, r, cols, mk<R>(1, 0), X, s->sX, cols, W, s->sU, r, mk<R>(0, 0), A,
                     s->sstride[q], r, b.nb));
-      TRY(finish_split<R>(s, b, A, s->sstride[q], (long long)rows * r, X, s->sX, countX));
+      const SplitProduct<R> px{OP_N, OP_C, rows, cols, r, A, s->sstride[q], r, W, s->sU, r};   // A' W^H
+      TRY(finish_split<R>(s, b, A, s->sstride[q], (long long)rows * r, X, s->sX, countX, &px));
     }
   }
   return NNE_OK;
@@ -505,12 +584,13 @@ nne_status compress(nne_state* s, int chi_new) {
       CTRY(copy_batched<R>(st, M, s->sstride[k], Xs, s->sX, (long long)rows * dr, b.nb));
       CTRY(cgemm<R>(st, OP_N, OP_C, rows, rows, dr, mk<R>(1, 0), Xs, s->sX, dr, Xs, s->sX, dr, mk<R>(0, 0), Hm,
                     s->sH, rows, b.nb));
-      CTRY(eigh_top<R>(st, Hm, s->sH, rows, r, W, s->sU, eigcx<R>(s, b), eigre<R>(s, b), eigu8(s, b), b.nb, s->d_err));
+      TRY(eigh_state<R>(s, b, Hm, s->sH, rows, r, W, s->sU));
       CTRY(fix_columns<R>(st, W, s->sU, rows, r, b.nb));
       CTRY(copy_batched<R>(st, W, s->sU, M, s->sstride[k], (long long)rows * r, b.nb));
       CTRY(cgemm<R>(st, OP_C, OP_N, r, dr, rows, mk<R>(1, 0), W, s->sU, r, Xs, s->sX, dr, mk<R>(0, 0), Cm, s->sR, dr,
                     b.nb));
-      TRY(finish_split<R>(s, b, Cm, s->sR, (long long)r * dr, Xs, s->sX, (long long)rows * dr));
+      const SplitProduct<R> px{OP_N, OP_N, rows, dr, r, W, s->sU, r, Cm, s->sR, dr};   // W C
+      TRY(finish_split<R>(s, b, Cm, s->sR, (long long)r * dr, Xs, s->sX, (long long)rows * dr, &px));
       cx<R>* N = spb<R>(s, b, k + 1);
       cx<R>* tmp = wsb<R>(s->T, s->sT, b);
       CTRY(cgemm<R>(st, OP_N, OP_N, r, 4 * dn, dr, mk<R>(1, 0), Cm, s->sR, dr, N, s->sstride[k + 1], 4 * dn,
@@ -555,6 +635,12 @@ nne_status read_err(nne_state* s) {
   if (e != cudaSuccess) return set_cuda_error(e, "cudaMemcpyAsync", __FILE__, __LINE__);
   e = cudaStreamSynchronize(s->ctx->stream);
   if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+  if (t != 0 && te) {
+    // reported once: the word is cleared so that the next call starts clean
+    e = cudaMemsetAsync(te, 0, sizeof(int), s->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->ctx->stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "cudaMemsetAsync", __FILE__, __LINE__);
+  }
   if (h != 0) return set_error(h, "device-side failure status %d (non-finite or zero norm in a gate step)", h);
   if (t != 0) return set_error(t, "tensor-core GEMM reported status %d (a bounded wait expired)", t);
   return NNE_OK;
@@ -752,14 +838,14 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
   }
   // scalars
   void* p = nullptr;
-  if ((rc = s->mem.alloc(&p, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64)) != NNE_OK)
+  if ((rc = s->mem.alloc(&p, sizeof(double) * (3 * n_inst + 3 * (size_t)n_inst * PARTS) + 64)) != NNE_OK)
     return fail(rc);
-  cudaMemsetAsync(p, 0, sizeof(double) * (3 * n_inst + 2 * (size_t)n_inst * PARTS) + 64, ctx->stream);
+  cudaMemsetAsync(p, 0, sizeof(double) * (3 * n_inst + 3 * (size_t)n_inst * PARTS) + 64, ctx->stream);
   s->d_lognorm = reinterpret_cast<double*>(p);
   s->d_logfid = s->d_lognorm + n_inst;
   s->d_scale = s->d_logfid + n_inst;
   s->d_parts = s->d_scale + n_inst;
-  s->d_err = reinterpret_cast<int*>(s->d_parts + 2 * (size_t)n_inst * PARTS);
+  s->d_err = reinterpret_cast<int*>(s->d_parts + 3 * (size_t)n_inst * PARTS);
   // workspaces
   const long long D = s->dmax, N4 = 4 * D;
   s->sX = N4 * N4;
@@ -772,7 +858,7 @@ nne_status nne_create_state(nne_ctx* ctx, int n_qubits, int chi, int n_inst, nne
   if ((rc = s->mem.alloc(&s->U, (size_t)s->sU * n_inst * s->esz)) != NNE_OK) return fail(rc);
   if ((rc = s->mem.alloc(&s->T, (size_t)s->sT * n_inst * s->esz)) != NNE_OK) return fail(rc);
   if ((rc = s->mem.alloc(&s->Rm, (size_t)s->sR * n_inst * s->esz)) != NNE_OK) return fail(rc);
-  const EighWork ew = eigh_workspace((int)N4, (int)D);
+  const EighWork ew = eigh_workspace_state((int)N4, (int)D, dtype);
   const size_t rsz = s->esz / 2;
   s->eig_cx_pi = ew.cx_elems;
   s->eig_re_pi = ew.re_elems;
@@ -951,27 +1037,37 @@ nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* r
         last[o] = k;
       }
     }
+  // strings spanning three or more sites take the carried-vector kernel
+  std::vector<int> general;
+  for (int o = 0; o < n_obs; ++o)
+    if (first[o] >= 0 && last[o] - first[o] > 1) general.push_back(o);
+  const int n_general = (int)general.size();
   cudaStream_t s = st->ctx->stream;
-  void *dp = nullptr, *df = nullptr, *dl = nullptr, *dout = nullptr;
+  void *dp = nullptr, *df = nullptr, *dl = nullptr, *dout = nullptr, *dgen = nullptr, *dv = nullptr;
   const size_t bp = (size_t)std::max(n_obs, 1) * n, bf = sizeof(int) * std::max(n_obs, 1),
-               bo = sizeof(double) * 2 * (size_t)std::max(n_obs, 1) * st->n_inst;
+               bo = sizeof(double) * 2 * (size_t)std::max(n_obs, 1) * st->n_inst,
+               bv = sizeof(double) * 2 * 2 * 4 * (size_t)n * st->dmax * st->n_inst;
   NNE_CUDA_TRY(cudaMallocAsync(&dp, bp, s));
   NNE_CUDA_TRY(cudaMallocAsync(&df, bf, s));
   NNE_CUDA_TRY(cudaMallocAsync(&dl, bf, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dgen, bf, s));
   NNE_CUDA_TRY(cudaMallocAsync(&dout, bo, s));
+  NNE_CUDA_TRY(cudaMallocAsync(&dv, bv, s));
   std::vector<double> hout(2 * (size_t)std::max(n_obs, 1) * st->n_inst);
   cudaError_t e = cudaMemcpyAsync(st->d_dims, st->dims.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && n_obs > 0) e = cudaMemcpyAsync(dp, paulis, (size_t)n_obs * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(df, first.data(), bf, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dl, last.data(), bf, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && n_general > 0)
+    e = cudaMemcpyAsync(dgen, general.data(), sizeof(int) * n_general, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = st->dtype == NNE_C64
             ? expect_sweep<float>(s, n, st->d_dims, (const void* const*)st->d_site, st->d_stride, st->n_inst, st->dmax,
-                                  n_obs, (const uint8_t*)dp, (const int*)df, (const int*)dl, st->d_env,
-                                  st->d_envscale, (double*)dout)
+                                  n_obs, (const uint8_t*)dp, (const int*)df, (const int*)dl, (const int*)dgen,
+                                  n_general, st->d_env, st->d_envscale, (double*)dv, (double*)dout)
             : expect_sweep<double>(s, n, st->d_dims, (const void* const*)st->d_site, st->d_stride, st->n_inst,
-                                   st->dmax, n_obs, (const uint8_t*)dp, (const int*)df, (const int*)dl, st->d_env,
-                                   st->d_envscale, (double*)dout);
+                                   st->dmax, n_obs, (const uint8_t*)dp, (const int*)df, (const int*)dl,
+                                   (const int*)dgen, n_general, st->d_env, st->d_envscale, (double*)dv, (double*)dout);
   if (e == cudaSuccess && n_obs > 0)
     e = cudaMemcpyAsync(hout.data(), dout, sizeof(double) * 2 * (size_t)n_obs * st->n_inst, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && log_fid_out)
@@ -982,7 +1078,9 @@ nne_status nne_expect(nne_state* st, int n_obs, const uint8_t* paulis, double* r
   cudaFreeAsync(dp, s);
   cudaFreeAsync(df, s);
   cudaFreeAsync(dl, s);
+  cudaFreeAsync(dgen, s);
   cudaFreeAsync(dout, s);
+  cudaFreeAsync(dv, s);
   if (rc != NNE_OK) return rc;
   for (int i = 0; i < st->n_inst; ++i)
     for (int o = 0; o < n_obs; ++o) {
@@ -1099,6 +1197,9 @@ void nne_set_option(int option, int value) {
   if (option == NNE_OPT_TENSOR_CORES) set_tensor_cores(value);
   if (option == NNE_OPT_SUBBATCHES) g_substreams = value < 1 ? 1 : (value > 8 ? 8 : value);
   if (option == NNE_OPT_SERIAL_LAYERS) g_serial_layers = value ? 1 : 0;
+  if (option == NNE_OPT_EIG_FP64) g_eig_fp64 = value ? 1 : 0;
+  if (option == NNE_OPT_GEMM_TMA) set_gemm_tma(value);
+  if (option == NNE_OPT_TEST_WAIT_LIMIT) set_tc_wait_limit(value);
 }
 
 nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, const float* alpha, const void* A,
@@ -1117,7 +1218,12 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
   int* te = tc_error_ptr();
   if (te) NNE_CUDA_TRY(cudaMemcpyAsync(&t, te, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   NNE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  if (t != 0) return set_error(t, "tensor-core GEMM reported status %d", t);
+  if (t != 0) {
+    // reported once: the word is cleared so that the next call starts clean
+    NNE_CUDA_TRY(cudaMemsetAsync(te, 0, sizeof(int), ctx->stream));
+    NNE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return set_error(t, "tensor-core GEMM reported status %d (a bounded wait expired)", t);
+  }
   return NNE_OK;
 }
 

@@ -290,6 +290,8 @@ OPT_TENSOR_CORES = 0
 OPT_SUBBATCHES = 1
 OPT_SERIAL_LAYERS = 2
 OPT_EIG_FP64 = 3
+OPT_GEMM_TMA = 4
+OPT_TEST_WAIT_LIMIT = 5
 
 
 class State:

@@ -4,10 +4,13 @@
         random complex64 A (M x K), B (K x N), C on the device; nne_cgemm_c64
         (C = A B + 0.5 C) four times.
     python -m paper_2501_13237_gb300.profile_cases gate [CHI] [N_INST]
-        one saturated two-qubit gate step with randomized truncation
-        (bonds CHI, k = CHI + 64, one power iteration) on N_INST instances:
-        theta GEMM, range finder, QR panels, the (CHI+64)-dimensional
-        tridiagonalisation and the centre split, as in the bench's steps.
+        one saturated two-qubit gate step with the bench's truncation
+        (bonds CHI, subspace iteration with k = CHI + 128 columns and four
+        power iterations, Rayleigh-Ritz) on N_INST instances.
+    python -m paper_2501_13237_gb300.profile_cases sweep N CHI N_INST
+        a chain of N sites with every bond at CHI (random complex64 site
+        tensors, N_INST instances) and one expectation sweep over every
+        <Z_i> and <X_i X_i+1> (nne_expect), twice.
 
 Inputs are seeded and synthetic; nothing here is timed or checked.
 """
@@ -37,7 +40,7 @@ def gate(chi: int = 512, n_inst: int = 8) -> None:
     n, q = 14, 5
     ctx = nne.Context(0)
     st = nne.State(ctx, n, chi, n_inst, nne.C64, nne.TRUNC_RSVD)
-    st.set_sketch(wl.gaussian_sketch(4 * chi, chi + 64, 1).astype(np.complex64), 1)
+    st.set_sketch(wl.gaussian_sketch(4 * chi, chi + 128, 1).astype(np.complex64), 4)
     rng = np.random.default_rng(0)
 
     def rc(shape):
@@ -53,6 +56,24 @@ def gate(chi: int = 512, n_inst: int = 8) -> None:
     st.close()
 
 
+def sweep(n: int, chi: int, n_inst: int) -> None:
+    import workloads as wl
+    from . import nne
+    ctx = nne.Context(0)
+    rng = np.random.default_rng(0)
+    st = nne.State(ctx, n, chi, n_inst, nne.C64)
+    caps = [1] + [min(chi, 4 ** k, 4 ** (n - k)) for k in range(1, n)] + [1]
+    for k in range(n):
+        M = ((rng.standard_normal((caps[k], 4, caps[k + 1])) + 1j * rng.standard_normal((caps[k], 4, caps[k + 1])))
+             / np.sqrt(8.0 * caps[k])).astype(np.complex64)
+        for i in range(n_inst):
+            st.write_site(i, k, M)
+    paulis = wl.pauli_codes(wl.obs_z(n) + wl.obs_xx(n), n)
+    for _ in range(2):
+        st.expect(paulis)
+    st.close()
+
+
 if __name__ == "__main__":
     import os
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
@@ -62,6 +83,8 @@ if __name__ == "__main__":
         gemm(*args)
     elif what == "gate":
         gate(*args)
+    elif what == "sweep":
+        sweep(*args)
     else:
         raise SystemExit(f"unknown case {what}")
     print("ok")

@@ -78,17 +78,18 @@ def test_server_budget_serialises(ctx):
 
 def test_server_rsvd_job(ctx):
     from paper_2501_13237_gb300 import nne, runner
-    w = wl.Workload("r", wl.brickwork_circuit(10, 10, 5), wl.NoiseModel(depol2=0.02, amp_damp=0.01, dephase=0.01),
+    w = wl.Workload("r", wl.brickwork_circuit(10, 10, 3), wl.NoiseModel(depol2=0.02, amp_damp=0.01, dephase=0.01),
                     (1.0, 3.0), 16, wl.obs_z(10) + wl.obs_xx(10), 1.0, "exp")
-    om = wl.gaussian_sketch(4 * 16, 24, 9).astype(np.complex64)
-    job = runner.job_for(w, dtype=0, trunc=nne.TRUNC_RSVD, sketch=om, power_iters=1)
+    # subspace iteration (k = 3 chi, six power iterations) against the exact SVD truncation
+    om = wl.gaussian_sketch(4 * 16, 48, 9).astype(np.complex64)
+    job = runner.job_for(w, dtype=0, trunc=nne.TRUNC_RSVD, sketch=om, power_iters=6)
     srv = nne.Server(0, workers=1)
     r = srv.poll(srv.submit(job))
     srv.close()
     assert r["status"] == 0, r["error"]
     paulis = wl.pauli_codes(w.observables, w.n)
     for i in range(2):
-        ref = mps.run(w.circuit, w.rate_table()[i], 16, sketch=om.astype(np.complex128), power_iters=1)
+        ref = mps.run(w.circuit, w.rate_table()[i], 16)
         assert np.abs(r["values"][i] - ref.expect_codes(paulis).real).max() < 1e-4
 
 
