@@ -6,8 +6,8 @@ every gate followed by two-qubit depolarizing p = 5e-4*lambda, amplitude
 damping gamma = 1e-3*lambda and dephasing 5e-4*lambda on both qubits, 8 noise
 levels lambda = 1..8 run as 8 instances of one state, chi = 512, complex64
 (split-TF32 tensor-core GEMMs), the SVD truncation of Sec. 2.1.2 reached by
-subspace iteration (k = 640 columns, 4 power iterations, Rayleigh-Ritz),
-observables all <Z_i> and
+subspace iteration (k = 640 columns, 4 power iterations, Rayleigh-Ritz with
+a float64-quality eigensolve), observables all <Z_i> and
 <X_i X_i+1>, weighted log-linear extrapolation (exponential fallback) to
 lambda* = 1.  Synthetic inputs from workloads/ (no datasets).
 
@@ -299,9 +299,15 @@ def main():
     nne.set_option(nne.OPT_SERIAL_LAYERS, 1)
     ms_prof, _, prof, _ = timed(False, 1, prof=True)
     nne.set_option(nne.OPT_SERIAL_LAYERS, 0)
+    # the same steps with the truncation's eigensolve in float32 (NNE_OPT_EIG_FP64 = 0)
+    nne.set_option(nne.OPT_EIG_FP64, 0)
+    step(False)
+    ms_f32, _, _, units_f32 = timed(False, args.steps)
+    nne.set_option(nne.OPT_EIG_FP64, 1)
 
     value = units / (ms / 1e3)
     e2e = units_e2e / (ms_e2e / 1e3)
+    value_f32 = units_f32 / (ms_f32 / 1e3)
 
     # roofline for the dominant kernel class
     pk = peaks()
@@ -311,7 +317,7 @@ def main():
     roof = None
     fast_lat = gate_latencies(st, ctx, plan, cursor[0], rates_dev, 6)
     cpu = None
-    fp64 = check = pk_meas = None
+    fp64 = check = pk_meas = roof_gemm = None
     if rank == 0 and not args.no_checks:
         st.close()
         torch.cuda.empty_cache()
@@ -319,6 +325,7 @@ def main():
         check = prefix_check(ctx, w, plan, snap, rates, paulis)
         pk_meas = measure_peaks(dev)
         roof = roofline(dominant, prof, pk, pk_meas)
+        roof_gemm = roofline_of("gemm_tc", prof, pk_meas) if prof.get("gemm_tc", (0, 0, 0))[1] else None
         n_cpu = 3
         dt = cpu_oracle_steps(n_cpu)
         cpu = {"value": n_cpu / dt, "unit": "gate_steps/s", "cores": threads_used(), "kind": "oracle",
@@ -342,17 +349,23 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "n100_d30_chi512_8lambda", "chi": CHI, "n": w.n, "n_lambda": n_inst,
                            "truncation": (f"SVD truncation to chi (Sec. 2.1.2) by subspace iteration: k={SUBSPACE_COLS} "
-                                          f"columns, q={POWER_ITERS} power iterations, Rayleigh-Ritz (float32 eigensolve; "
-                                          "the float64 eigensolve variant in accuracy.fp64_eigensolve); complex64, "
-                                          "3xTF32 tensor-core GEMMs; <P> checked against the complex128 exact-SVD "
-                                          "path (accuracy)"),
+                                          f"columns, q={POWER_ITERS} power iterations, Rayleigh-Ritz with a "
+                                          "float64-quality eigensolve (double-float Householder reduction on the "
+                                          "float32 pipes, float64 bisection and inverse iteration); complex64, 3xTF32 "
+                                          "tensor-core GEMMs; <P> checked against the complex128 exact-SVD path "
+                                          "(accuracy); the same steps with a float32 eigensolve in float32_eigensolve"),
                            "step": f"{LAYERS_PER_STEP} saturated brickwork layers ({gates_per_step} gate steps) "
                                    "+ 199-observable sweep + fit",
                            "l2": "inputs larger than L2 (state ~6.7 GB)", "parallelism": f"replicas{world}"},
                 "e2e": {"value": e2e, "unit": "gate_steps/s", "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": int(launches), "roofline": roof, "roofline_gemm": roof_gemm, "cpu_baseline": cpu,
+                "clocks": clk,
                 "fp64_path": fp64, "fast_gate_latency_ms": fast_lat, "accuracy": check,
+                "float32_eigensolve": {"value": value_f32, "unit": "gate_steps/s", "steps": args.steps,
+                                       "ms_per_step": ms_f32 / args.steps,
+                                       "what": "the same timed steps with the truncation's eigensolve in float32 "
+                                               "(NNE_OPT_EIG_FP64 = 0); its <P> error in accuracy.float32_eigensolve"},
                 "measured_peaks": pk_meas,
                 "kernel_classes_ms": prof_summary, "serving": serving, "batch": batch}
         print(json.dumps(line), flush=True)
@@ -366,6 +379,11 @@ ALU_CLASSES = {"gemm": "float32 SIMT GEMMs", "wy_apply": "split-K block-reflecto
                "qr_factor": "Householder panel factorisation", "tridiag": "Hermitian tridiagonalisation"}
 
 
+def roofline_of(name, prof, meas):
+    t_ms, count, work = prof[name]
+    return roofline((name, (t_ms, count, work)), prof, None, meas)
+
+
 def roofline(dominant, prof, pk, meas):
     """Roofline entry of the dominant kernel class, from live CUDA-event timing.
 
@@ -374,8 +392,10 @@ def roofline(dominant, prof, pk, meas):
     over the timed region / the class's summed launch time.  Tensor-core GEMMs
     (complex64 as three TF32 products per real product) take the TF32 peak
     measured in this run with torch.matmul, sustained (the class is timed inside
-    a seconds-long step); the others run on the FP32 pipes and take the derived
-    FP32 SIMT peak."""
+    a seconds-long step); the float64 tridiagonalisation takes the float64
+    matmul rate measured in this run; the others run on the FP32 pipes and take
+    the derived FP32 SIMT peak.  `roofline_gemm` in the line is the same entry
+    for the tensor-core GEMM class whatever the dominant class is."""
     name, (t_ms, count, work) = dominant
     if count == 0 or t_ms <= 0:
         return None
@@ -388,6 +408,12 @@ def roofline(dominant, prof, pk, meas):
                     "peak_source": "measured in this run: torch.matmul float32 with TF32, 8192^3, back to back "
                                    "for 2 s (sustained); complex64 runs as 3 TF32 products per real product, so "
                                    "at most 1/3 of it is algorithmic"})
+    elif name == "tridiag" and achieved is not None:
+        # the float64 Householder reduction of the complex64 path's Rayleigh-Ritz matrix
+        peak = meas["fp64_tflops"]
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "what": "Hermitian tridiagonalisation in float64 ((16/3) n^3 flops per matrix)",
+                    "peak_source": "measured in this run: torch.matmul float64 4096^3 (float64 pipes)"})
     elif name in ALU_CLASSES and achieved is not None:
         out.update({"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "what": ALU_CLASSES[name],
@@ -477,9 +503,9 @@ def prefix_check(ctx, w, plan, snap, rates, paulis):
     lev = list(snap["levels"])
     G = ctx.build_superops(np.ascontiguousarray(us[:CHECK_GATES]), np.ascontiguousarray(rates[lev]))
     out, secs = {}, {}
-    for name, dt, tr, k, q, e in (("c128", nne.C128, nne.TRUNC_EXACT, None, None, 0),
-                                  ("fast", nne.C64, nne.TRUNC_RSVD, SUBSPACE_COLS, POWER_ITERS, 0),
-                                  ("fast_fp64_eig", nne.C64, nne.TRUNC_RSVD, SUBSPACE_COLS, POWER_ITERS, 1)):
+    for name, dt, tr, k, q, e in (("c128", nne.C128, nne.TRUNC_EXACT, None, None, 1),
+                                  ("fast", nne.C64, nne.TRUNC_RSVD, SUBSPACE_COLS, POWER_ITERS, 1),
+                                  ("fast_fp32_eig", nne.C64, nne.TRUNC_RSVD, SUBSPACE_COLS, POWER_ITERS, 0)):
         nne.set_option(nne.OPT_EIG_FP64, e)
         s = restore(ctx, nne, w, snap, list(range(len(lev))), dt, tr, k, q)
         torch.cuda.synchronize()
@@ -489,20 +515,19 @@ def prefix_check(ctx, w, plan, snap, rates, paulis):
         secs[name] = time.perf_counter() - t0
         out[name] = s.expect(paulis)
         s.close()
-        nne.set_option(nne.OPT_EIG_FP64, 0)
+        nne.set_option(nne.OPT_EIG_FP64, 1)
         torch.cuda.empty_cache()
     err = np.abs(out["fast"][0].real - out["c128"][0].real)
-    err64 = np.abs(out["fast_fp64_eig"][0].real - out["c128"][0].real)
+    err32 = np.abs(out["fast_fp32_eig"][0].real - out["c128"][0].real)
     steps = CHECK_GATES * len(lev)
     return {"max_abs_err_P": float(err.max()), "mean_abs_err_P": float(err.mean()),
             "dlogF": (out["fast"][1] - out["c128"][1]).tolist(), "prefix_gates": CHECK_GATES,
             "levels_lambda": [float(w.lambdas[i]) for i in lev], "n_obs": int(paulis.shape[0]),
             "vs": "complex128 exact-SVD path on the GPU, same saturated state",
-            "fp64_eigensolve": {"max_abs_err_P": float(err64.max()),
-                                "dlogF": (out["fast_fp64_eig"][1] - out["c128"][1]).tolist(),
-                                "gate_steps_per_s_prefix": steps / secs["fast_fp64_eig"],
-                                "what": "the same fast path with the Rayleigh-Ritz eigensolve's reduction, "
-                                        "bisection and inverse iteration in float64 (NNE_OPT_EIG_FP64)"},
+            "float32_eigensolve": {"max_abs_err_P": float(err32.max()),
+                                   "dlogF": (out["fast_fp32_eig"][1] - out["c128"][1]).tolist(),
+                                   "what": "the same path with the Rayleigh-Ritz eigensolve in float32 "
+                                           "(NNE_OPT_EIG_FP64 = 0)"},
             "gate_steps_per_s_prefix": {k2: steps / v for k2, v in secs.items()}}
 
 
@@ -554,12 +579,15 @@ def serving_run(n_requests: int, rate_per_s: float, seed: int, workers: int, dev
     """Open-loop request stream through nne_submit / nne_poll: Poisson arrivals,
     requests drawn like the serving workload at reduced sizes (n in [8, 32],
     depth in [5, 20], chi in {16, 32, 64, 128}, 4-8 levels, random channel mix,
-    all <Z_i>, complex64, exact truncation).  Latency = completion - arrival."""
+    all <Z_i>, complex64, exact truncation with the float32 eigensolve: at these bonds
+    the float64 reduction of a 512-wide Gram matrix takes the slow path and the
+    float32 one meets the 1e-4 budget).  Latency = completion - arrival."""
     import workloads as wl
     from paper_2501_13237_gb300 import nne, replicas, runner
     reqs = wl.serving_stream(seed, n_requests, rate_per_s, n_range=(8, 32), depth_range=(5, 20),
                              chis=(16, 32, 64, 128))
     jobs = [runner.job_for(r.workload, dtype=nne.C64) for r in reqs]
+    nne.set_option(nne.OPT_EIG_FP64, 0)
     srv = nne.Server(device, hbm_budget_bytes=150 << 30, workers=workers)
     t0 = time.perf_counter()
     tickets = []
@@ -570,6 +598,7 @@ def serving_run(n_requests: int, rate_per_s: float, seed: int, workers: int, dev
         tickets.append(srv.submit(j))
     res = [srv.poll(t) for t in tickets]
     srv.close()
+    nne.set_option(nne.OPT_EIG_FP64, 1)
     bad = [r for r in res if r["status"] != 0]
     lat = np.array([r["t_end"] - r["t_submit"] for r in res])
     span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
@@ -577,29 +606,31 @@ def serving_run(n_requests: int, rate_per_s: float, seed: int, workers: int, dev
     return {"requests": n_requests, "offered_per_s": rate_per_s, "workers": workers, "failed": len(bad),
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "requests_per_s": n_requests / span, "gate_steps_per_s": steps / span,
-            "sizes": "n 8-32, depth 5-20, chi 16-128, 4-8 levels, c64 exact truncation"}
+            "sizes": "n 8-32, depth 5-20, chi 16-128, 4-8 levels, c64 exact truncation, float32 eigensolve"}
 
 
 def batch_run(n_circuits: int, workers: int, device: int = 0):
     """The 64-circuit batch workload (n ~ U[16,64], depth ~ U[10,40], chi in
     {32, 64, 128}, 5 levels of depolarizing + dephasing, all <Z_i>, exponential
-    fit; complex64, exact truncation) submitted at once to a server with
+    fit; complex64, exact truncation, float32 eigensolve) submitted at once to a server with
     `workers` streams: wall time from the first submit to the last completion."""
     import workloads as wl
     from paper_2501_13237_gb300 import nne, runner
     ws = wl.batch64(0, n_circuits)
     jobs = [runner.job_for(w, dtype=nne.C64) for w in ws]
+    nne.set_option(nne.OPT_EIG_FP64, 0)
     srv = nne.Server(device, hbm_budget_bytes=150 << 30, workers=workers)
     t0 = time.perf_counter()
     tickets = [srv.submit(j) for j in jobs]
     res = [srv.poll(t) for t in tickets]
     wall = time.perf_counter() - t0
     srv.close()
+    nne.set_option(nne.OPT_EIG_FP64, 1)
     steps = sum(r["gate_steps"] for r in res)
     return {"circuits": n_circuits, "workers": workers, "failed": sum(r["status"] != 0 for r in res),
             "wall_s": wall, "gate_steps": int(steps), "gate_steps_per_s": steps / wall,
             "circuits_per_s": n_circuits / wall,
-            "sizes": "n 16-64, depth 10-40, chi 32/64/128, 5 levels, c64 exact truncation"}
+            "sizes": "n 16-64, depth 10-40, chi 32/64/128, 5 levels, c64 exact truncation, float32 eigensolve"}
 
 
 if __name__ == "__main__":

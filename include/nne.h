@@ -270,22 +270,31 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
  * NNE_OPT_SERIAL_LAYERS (default 0): when 1, nne_apply_layer runs all of a
  * state's instances as one batch on the context stream, whatever the state's
  * sub-batch count -- for per-launch timing of the kernels alone.
- * NNE_OPT_EIG_FP64 (default 0): when 1, complex64 states solve the
- * truncation's Hermitian eigenproblems (the Gram matrix of the exact
- * truncation, the Rayleigh-Ritz matrix of the subspace iteration, the centre
- * compression) with the Householder reduction, bisection and inverse
- * iteration in float64 and the back-transformation in float32; 0 runs them
- * in float32.  complex128 states always use float64.
- * NNE_OPT_GEMM_TMA (default 1): large complex64 GEMMs (M >= 128, N >= 64,
+ * NNE_OPT_EIG_FP64 (default 1): complex64 states solve the truncation's
+ * Hermitian eigenproblems (the Gram matrix of the exact truncation, the
+ * Rayleigh-Ritz matrix of the subspace iteration, the centre compression)
+ * with float64 quality: the Householder reduction in float64 (matrices that
+ * fit a cluster's shared memory) or in double-float arithmetic on the
+ * float32 pipes (larger ones; about 2^-46 relative), bisection and inverse
+ * iteration in float64, the back-transformation in float32; 0 runs them in
+ * float32 (about 1.5x the gate-step rate at chi = 512, with a float32
+ * reduction's error of eps_32 times the largest eigenvalue, which turns the
+ * eigenvectors next to a flat cut).  complex128 states always use float64.
+ * NNE_OPT_GEMM_TMA (default 2): large complex64 GEMMs (M >= 128, N >= 64,
  * K >= 64) split their operands once into TF32 planes and run the TMA-fed
- * tcgen05 kernel; 0 keeps the earlier tensor-core kernel that splits inside
- * its producer warps (for comparisons).
+ * tcgen05 kernel, with 128-byte swizzled K rows in 2 stages (1) or 64-byte
+ * rows in 4 stages (2, the default kernel); 0 keeps the earlier tensor-core
+ * kernel that splits inside its producer warps (for comparisons).
  * NNE_OPT_TEST_WAIT_LIMIT (test hook, default 0): bound, in polls, of the
  * TMA GEMM's pipeline mbarrier waits; 0 is the default bound, a negative
  * value makes every such wait expire at once.  An expired wait makes the
  * kernel record NNE_ERR_TIMEOUT (reported once by the next nne_sync or
  * nne_cgemm_c64, then cleared) and return after waiting, with the full
  * bound, for its own copies and MMAs.
+ * NNE_OPT_SWEEP_CLUSTER (default 0): CTAs per cluster of nne_expect's
+ * environment sweep; 0 picks the size that covers the most SMs in the fewest
+ * waves (occupancy query of each size), 1..16 forces a size (for tests and
+ * comparisons; a size the GPU cannot schedule makes nne_expect fail).
  * Options are process-wide; set them while no other thread calls the library. */
 #define NNE_OPT_TENSOR_CORES 0
 #define NNE_OPT_SUBBATCHES 1
@@ -293,6 +302,7 @@ nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, 
 #define NNE_OPT_EIG_FP64 3
 #define NNE_OPT_GEMM_TMA 4
 #define NNE_OPT_TEST_WAIT_LIMIT 5
+#define NNE_OPT_SWEEP_CLUSTER 6
 void nne_set_option(int option, int value);
 
 /* Wait for the state's enqueued work; returns the first device-side error. */

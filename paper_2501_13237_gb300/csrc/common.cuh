@@ -23,6 +23,31 @@ template <typename R> __host__ __device__ __forceinline__ cx<R> operator*(cx<R> 
 template <typename R> __host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk(s * a.re, s * a.im); }
 template <typename R> __host__ __device__ __forceinline__ cx<R> conj(cx<R> a) { return mk(a.re, -a.im); }
 template <typename R> __host__ __device__ __forceinline__ R norm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// |a|^2 in float64 whatever R.
+template <typename R> __host__ __device__ __forceinline__ double norm2d(cx<R> a) {
+  return (double)a.re * (double)a.re + (double)a.im * (double)a.im;
+}
+// Phase of a reflector pivot.  complex64 entries below ~1e-19 have denormal
+// (few-bit) or zero float32 squares, so |x0| taken from x0.re^2 + x0.im^2 is
+// wrong there, |alpha| differs from ||x|| and the reflector built from it is
+// not unitary (a Clifford circuit's tensors, scaled permutations plus rounding
+// noise down to 1e-24, hit this).  The phase is taken from x0 / max(|re|, |im|):
+// x0 = ax0 (pr + i pi) with |pr + i pi| = 1 to rounding; (1, 0) and 0 for x0 = 0.
+template <typename R, typename T>
+__host__ __device__ __forceinline__ void unit_phase_of(cx<R> x0, T* pr, T* pi, T* ax0) {
+  const T s = fmax(fabs((T)x0.re), fabs((T)x0.im));
+  if (!(s > T(0))) {
+    *pr = T(1);
+    *pi = T(0);
+    *ax0 = T(0);
+    return;
+  }
+  const T a = (T)x0.re / s, b = (T)x0.im / s;
+  const T r = sqrt(a * a + b * b);
+  *pr = a / r;
+  *pi = b / r;
+  *ax0 = s * r;
+}
 // a += b * c
 template <typename R> __host__ __device__ __forceinline__ void fma_(cx<R>& a, cx<R> b, cx<R> c) {
   a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
@@ -72,7 +97,7 @@ namespace nne {
 enum ProfClass {
   K_GEMM = 0, K_SUPEROP_APPLY = 1, K_TRIDIAG = 2, K_BISECT = 3, K_INVITER = 4, K_BACKTRANSFORM = 5,
   K_QR_FACTOR = 6, K_WY = 7, K_ELEMWISE = 8, K_SWEEP_ENV = 9, K_SWEEP_OBS = 10, K_SUPEROP_BUILD = 11,
-  K_FIT = 12, K_GEMM_TC = 13, PROF_CLASSES = 16
+  K_FIT = 12, K_GEMM_TC = 13, K_BISECT64 = 14, PROF_CLASSES = 16
 };
 class ProfScope {
  public:

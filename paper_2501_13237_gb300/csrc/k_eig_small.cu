@@ -38,11 +38,12 @@ __device__ __forceinline__ void tridiag_publish(const cx<R>* Hl_row, int n, int 
     R xn2 = 0;
     for (int w2 = 0; w2 < nw; ++w2) xn2 += red[w2];
     const cx<R> x0 = conj(Hl_row[r + 1]);
-    const R ax0 = sqrt(norm2(x0)), xn = sqrt(xn2);
+    R pr, pi, ax0;
+    unit_phase_of(x0, &pr, &pi, &ax0);
+    const R xn = sqrt(xn2);
     cx<R> alpha = mk<R>(0, 0);
     R un = 0;
     if (xn > R(0)) {
-      const R pr = ax0 > R(0) ? x0.re / ax0 : R(1), pi = ax0 > R(0) ? x0.im / ax0 : R(0);
       alpha = mk<R>(-xn * pr, -xn * pi);
       un = sqrt(R(2) * xn2 + R(2) * xn * ax0);
     }

@@ -87,11 +87,12 @@ __global__ void __launch_bounds__(QR_THREADS) qr_panel_kernel(cx<R>* Ab, long lo
   auto pivot = [&]() {
     const double xn2 = xn2_s;
     const cx<R> x0 = x0_s;
-    const double ax0 = sqrt((double)norm2(x0)), xn = sqrt(xn2);
+    double pr, pi, ax0;
+    unit_phase_of(x0, &pr, &pi, &ax0);
+    const double xn = sqrt(xn2);
     cx<R> alpha = mk<R>(0, 0);
     double un = 0;
     if (xn > 0) {
-      const double pr = ax0 > 0 ? (double)x0.re / ax0 : 1.0, pi = ax0 > 0 ? (double)x0.im / ax0 : 0.0;
       alpha = mk<R>((R)(-xn * pr), (R)(-xn * pi));
       un = sqrt(2.0 * xn2 + 2.0 * xn * ax0);
     }
@@ -292,14 +293,16 @@ struct PanelShared {
 
 // Reflector pivot from the squared norm xn2 of the column at and below the
 // diagonal and its diagonal entry x0: alpha = -e^{i arg x0} ||x||,
-// un = ||x - alpha e_0||, tau = 2 (0 for a zero column).  Evaluated in R.
+// un = ||x - alpha e_0||, tau = 2 (0 for a zero column).  Evaluated in R,
+// the phase of x0 by unit_phase_of.
 template <typename R>
 __device__ __forceinline__ void hh_pivot(R xn2, cx<R> x0, cx<R>* alpha, R* inv, R* tau) {
-  const R ax0 = sqrt(norm2(x0)), xn = sqrt(xn2);
+  R pr, pi, ax0;
+  unit_phase_of(x0, &pr, &pi, &ax0);
+  const R xn = sqrt(xn2);
   cx<R> a = mk<R>(0, 0);
   R un = 0;
   if (xn > R(0)) {
-    const R pr = ax0 > R(0) ? x0.re / ax0 : R(1), pi = ax0 > R(0) ? x0.im / ax0 : R(0);
     a = mk<R>(-xn * pr, -xn * pi);
     un = sqrt(R(2) * xn2 + R(2) * xn * ax0);
   }

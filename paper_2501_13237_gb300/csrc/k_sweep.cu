@@ -23,6 +23,9 @@
 // then added into float64 accumulators.  Each environment is rescaled to
 // max-abs 1 and its log-scale carried separately, so long chains neither
 // overflow nor underflow.
+#include <map>
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace cg = cooperative_groups;
@@ -53,7 +56,8 @@ __device__ __forceinline__ T block_max(T v, T* red) {
 namespace sweep {
 
 constexpr int THREADS = 256;
-constexpr int NB = 8;   // loads in flight per thread and batch; also the float32 run length before a float64 fold
+constexpr int NB = 8;            // loads per thread and batch; also the float32 run length before a float64 fold
+constexpr int RING_STAGES = 4;   // batches in flight per thread (cp.async ring in shared memory)
 
 // Elements of one 16-byte load: two complex64 or one complex128.
 template <typename R> struct Vec;
@@ -80,6 +84,30 @@ __device__ __forceinline__ void ldv<double, 1>(const cx<double>* p, cx<double>* 
   o[0] = mk<double>(v.x, v.y);
 }
 
+// Asynchronous global -> shared copy of one load unit (16 bytes, or 8 for a
+// single complex64); bytes past `valid` are zero-filled.
+template <int BYTES>
+__device__ __forceinline__ void cp_unit(uint32_t dst, const void* src, bool valid) {
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_ring() { asm volatile("cp.async.wait_group %0;" ::"n"(RING_STAGES - 1) : "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// This thread's slot i of ring stage st (16-byte slots, threads interleaved).
+__device__ __forceinline__ uint32_t ring_slot(uint32_t ring, int st, int i) {
+  return ring + (uint32_t)(((st * NB + i) * THREADS + (int)threadIdx.x) * 16);
+}
+template <typename R, int V>
+__device__ __forceinline__ void ring_read(const unsigned char* ring_ptr, int st, int i, cx<R>* o) {
+  const unsigned char* p = ring_ptr + ((st * NB + i) * THREADS + threadIdx.x) * 16;
+#pragma unroll
+  for (int v = 0; v < V; ++v) o[v] = reinterpret_cast<const cx<R>*>(p)[v];
+}
+
 __device__ __forceinline__ cx<double> up(cx<float> a) { return mk<double>(a.re, a.im); }
 __device__ __forceinline__ cx<double> up(cx<double> a) { return a; }
 
@@ -92,7 +120,9 @@ struct Layout {
   __host__ __device__ int part() const { return D + 6 * SL; }       // 2 x THREADS: row-group partial sums
   __host__ __device__ int scal() const { return D + 6 * SL + 2 * THREADS; }   // 8 doubles (maxes, reduction)
   __host__ __device__ int coef() const { return scal() + 8; }       // D x cx<R>: environment in the state's precision
-  __host__ __device__ size_t bytes(size_t esz) const { return 16 * (size_t)coef() + esz * (size_t)D; }
+  // per-thread rings of asynchronous copies (RING_STAGES x NB 16-byte slots per thread), 16-byte aligned
+  __host__ __device__ size_t ring_off(size_t esz) const { return (16 * (size_t)coef() + esz * (size_t)D + 15) & ~size_t(15); }
+  __host__ __device__ size_t bytes(size_t esz) const { return ring_off(esz) + (size_t)RING_STAGES * NB * THREADS * 16; }
 };
 
 __host__ __device__ inline int slice_cap(int D, int cs) { return (D + cs - 1) / cs + 2; }
@@ -108,9 +138,14 @@ __device__ __forceinline__ double block_max_sw(double v, double* red) {
 }
 
 // Left pass at one site: fin[s][j] = sum_a coef[a] M[a][s][b0 + j] for this CTA's columns.
+// Thread (unit u, row group g) streams the rows a = g, g + G, ... of its unit
+// through its own ring of asynchronous copies, RING_STAGES batches of NB rows
+// in flight.
 template <typename R, int V>
 __device__ void left_site(const cx<R>* __restrict__ M, int dl, int dr, int b0, int w, const cx<R>* coef,
-                          cx<double>* fin, int SL, cx<double>* part) {
+                          cx<double>* fin, int SL, cx<double>* part, unsigned char* ring_ptr) {
+  constexpr int BYTES = (int)sizeof(cx<R>) * V;
+  const uint32_t ring = (uint32_t)__cvta_generic_to_shared(ring_ptr);
   const int t = threadIdx.x;
   const int wu = w / V, U = 4 * wu;
   if (U == 0) return;
@@ -124,36 +159,41 @@ __device__ void left_site(const cx<R>* __restrict__ M, int dl, int dr, int b0, i
     if (act) {
       const int s = u / wu, j = (u % wu) * V;
       const cx<R>* col = M + (long long)s * dr + b0 + j;
-      const long long rs = 4LL * dr * G;   // row step of this group
-      int a = g;
-      const cx<R>* p = col + (long long)a * 4 * dr;
-      while (a < dl) {
-        cx<R> m[NB][V];
-        cx<R> c[NB];
+      const long long rs = 4LL * dr * G;   // element step between this thread's rows
+      const int nrows = (dl - g + G - 1) / G;
+      const int nbatch = (nrows + NB - 1) / NB;
+      auto issue = [&](int bi) {
+        if (bi < nbatch) {
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          const int ai = a + i * G;
-          if (ai < dl) {
-            ldv<R, V>(p + i * rs, m[i]);
-            c[i] = coef[ai];
-          } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) m[i][v] = mk<R>(0, 0);
-            c[i] = mk<R>(0, 0);
+          for (int i = 0; i < NB; ++i) {
+            const int ri = bi * NB + i;
+            const bool ok = ri < nrows;
+            cp_unit<BYTES>(ring_slot(ring, bi % RING_STAGES, i), ok ? col + (long long)g * 4 * dr + ri * rs : col, ok);
           }
         }
+        cp_commit();
+      };
+#pragma unroll
+      for (int b = 0; b < RING_STAGES - 1; ++b) issue(b);
+      for (int bi = 0; bi < nbatch; ++bi) {
+        issue(bi + RING_STAGES - 1);
+        cp_wait_ring();
         cx<R> s32[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) s32[v] = mk<R>(0, 0);
 #pragma unroll
-        for (int i = 0; i < NB; ++i)
+        for (int i = 0; i < NB; ++i) {
+          const int ri = bi * NB + i;
+          cx<R> m[V];
+          ring_read<R, V>(ring_ptr, bi % RING_STAGES, i, m);
+          const cx<R> c = ri < nrows ? coef[g + ri * G] : mk<R>(0, 0);
 #pragma unroll
-          for (int v = 0; v < V; ++v) fma_(s32[v], c[i], m[i][v]);
+          for (int v = 0; v < V; ++v) fma_(s32[v], c, m[v]);
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v] = acc[v] + up(s32[v]);
-        a += NB * G;
-        p += NB * rs;
       }
+      cp_wait_all();
     }
     if (G == 1) {
       if (act) {
@@ -182,49 +222,69 @@ __device__ void left_site(const cx<R>* __restrict__ M, int dl, int dr, int b0, i
 
 // Right pass at one site: rho[tt][a] = sum_b M[a][tt][b] coef[b] for this CTA's rows, one warp per row.
 // Writes rho to global memory and R[a] = rho[0][a] + rho[3][a] into the slice; returns the row max-abs.
+// A warp's work is a flat list of jobs (row, segment tt, batch of 32 NB units),
+// streamed through each lane's ring of asynchronous copies.
 template <typename R, int V>
 __device__ double right_site(const cx<R>* __restrict__ M, int dr, int a0, int a1, const cx<R>* coef, cx<double>* rho,
-                             int D, cx<double>* slice) {
+                             int D, cx<double>* slice, unsigned char* ring_ptr) {
+  constexpr int BYTES = (int)sizeof(cx<R>) * V;
+  const uint32_t ring = (uint32_t)__cvta_generic_to_shared(ring_ptr);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = THREADS / 32;
-  const int nu = dr / V;   // units per segment
-  double mx = 0;
-  for (int a = a0 + warp; a < a1; a += nw) {
-    const cx<R>* row = M + (long long)a * 4 * dr;
-    cx<double> acc[4];
+  const int nu = dr / V;                                   // units per segment
+  const int nbs = (nu + 32 * NB - 1) / (32 * NB);          // batches per segment
+  const int rows_w = a1 - a0 > warp ? (a1 - a0 - warp + nw - 1) / nw : 0;
+  const int jobs = rows_w * 4 * nbs;
+  auto job_src = [&](int jb, int i, bool& ok) -> const cx<R>* {
+    const int ri = jb / (4 * nbs), rem = jb % (4 * nbs), tt = rem / nbs, bb = rem % nbs;
+    const int a = a0 + warp + ri * nw;
+    const int uu = bb * 32 * NB + lane + 32 * i;
+    ok = uu < nu;
+    return M + ((long long)a * 4 + tt) * dr + (ok ? uu * V : 0);
+  };
+  auto issue = [&](int jb) {
+    if (jb < jobs) {
 #pragma unroll
-    for (int tt = 0; tt < 4; ++tt) {
-      acc[tt] = mk<double>(0, 0);
-      const cx<R>* seg = row + (long long)tt * dr;
-      for (int base = 0; base < nu; base += 32 * NB) {
-        cx<R> m[NB][V];
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          const int uu = base + lane + 32 * i;
-          if (uu < nu) ldv<R, V>(seg + uu * V, m[i]);
-          else
-#pragma unroll
-            for (int v = 0; v < V; ++v) m[i][v] = mk<R>(0, 0);
-        }
-        cx<R> s32 = mk<R>(0, 0);
-#pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          const int uu = base + lane + 32 * i;
-          if (uu < nu)
-#pragma unroll
-            for (int v = 0; v < V; ++v) fma_(s32, m[i][v], coef[uu * V + v]);
-        }
-        acc[tt] = acc[tt] + up(s32);
+      for (int i = 0; i < NB; ++i) {
+        bool ok;
+        const cx<R>* src = job_src(jb, i, ok);
+        cp_unit<BYTES>(ring_slot(ring, jb % RING_STAGES, i), src, ok);
       }
-      acc[tt] = warp_sum(acc[tt]);
     }
-    if (lane == 0) {
+    cp_commit();
+  };
 #pragma unroll
-      for (int tt = 0; tt < 4; ++tt) rho[(long long)tt * D + a] = acc[tt];
-      const cx<double> Ra = acc[0] + acc[3];
-      slice[a - a0] = Ra;
-      mx = fmax(mx, fmax(fabs(Ra.re), fabs(Ra.im)));
+  for (int b = 0; b < RING_STAGES - 1; ++b) issue(b);
+  double mx = 0;
+  cx<double> acc = mk<double>(0, 0), seg0 = mk<double>(0, 0);
+  for (int jb = 0; jb < jobs; ++jb) {
+    issue(jb + RING_STAGES - 1);
+    cp_wait_ring();
+    const int ri = jb / (4 * nbs), rem = jb % (4 * nbs), tt = rem / nbs, bb = rem % nbs;
+    cx<R> s32 = mk<R>(0, 0);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int uu = bb * 32 * NB + lane + 32 * i;
+      cx<R> m[V];
+      ring_read<R, V>(ring_ptr, jb % RING_STAGES, i, m);
+      if (uu < nu)
+#pragma unroll
+        for (int v = 0; v < V; ++v) fma_(s32, m[v], coef[uu * V + v]);
+    }
+    acc = acc + up(s32);
+    if (bb == nbs - 1) {   // segment tt of row a complete
+      const cx<double> tot = warp_sum(acc);
+      acc = mk<double>(0, 0);
+      const int a = a0 + warp + ri * nw;
+      if (lane == 0) rho[(long long)tt * D + a] = tot;
+      if (tt == 0) seg0 = tot;
+      if (tt == 3 && lane == 0) {
+        const cx<double> Ra = seg0 + tot;
+        slice[a - a0] = Ra;
+        mx = fmax(mx, fmax(fabs(Ra.re), fabs(Ra.im)));
+      }
     }
   }
+  cp_wait_all();
   return mx;
 }
 
@@ -252,6 +312,7 @@ __global__ void __launch_bounds__(sweep::THREADS) env_cluster_kernel(int n, cons
   cx<double>* part = base + L.part();
   double* scal = reinterpret_cast<double*>(base + L.scal());   // [0..1] maxes (double-buffered), [8..15] reduction
   cx<R>* coef = reinterpret_cast<cx<R>*>(base + L.coef());
+  unsigned char* ring_ptr = smem_raw + L.ring_off(sizeof(cx<R>));
   cx<double>* E = reinterpret_cast<cx<double>*>(env) + ((long long)z * 2 + pass) * (n + 1) * D;
   double* ls = envscale + ((long long)z * 2 + pass) * (n + 1);
   cx<double>* VK = reinterpret_cast<cx<double>*>(vecs) + ((long long)z * 2 + pass) * n * 4 * D;
@@ -281,8 +342,8 @@ __global__ void __launch_bounds__(sweep::THREADS) env_cluster_kernel(int n, cons
       const int b0 = min(dr, rank * bs), b1 = min(dr, b0 + bs);
       own0 = b0;
       own1 = b1;
-      if (vec) left_site<R, VV>(M, dl, dr, b0, b1 - b0, coef, fin, L.SL, part);
-      else left_site<R, 1>(M, dl, dr, b0, b1 - b0, coef, fin, L.SL, part);
+      if (vec) left_site<R, VV>(M, dl, dr, b0, b1 - b0, coef, fin, L.SL, part, ring_ptr);
+      else left_site<R, 1>(M, dl, dr, b0, b1 - b0, coef, fin, L.SL, part, ring_ptr);
       __syncthreads();
       cx<double>* ell = VK + (long long)k * 4 * D;
       for (int q = t; q < 4 * (b1 - b0); q += THREADS) {
@@ -300,7 +361,8 @@ __global__ void __launch_bounds__(sweep::THREADS) env_cluster_kernel(int n, cons
       own0 = a0;
       own1 = a1;
       cx<double>* rho = VK + (long long)k * 4 * D;
-      mx = vec ? right_site<R, VV>(M, dr, a0, a1, coef, rho, D, sl) : right_site<R, 1>(M, dr, a0, a1, coef, rho, D, sl);
+      mx = vec ? right_site<R, VV>(M, dr, a0, a1, coef, rho, D, sl, ring_ptr)
+               : right_site<R, 1>(M, dr, a0, a1, coef, rho, D, sl, ring_ptr);
     }
     mx = block_max_sw(mx, scal + 8);
     if (t == 0) scal[pb] = mx;
@@ -485,12 +547,62 @@ __global__ void __launch_bounds__(256) obs_local_kernel(int n, const int* __rest
 }
 
 // Cluster size of the environment sweep: two clusters (left, right pass) per
-// instance; 16 CTAs per cluster while that keeps the grid within the GPU,
-// else 8; small bonds take fewer.
+// instance, one CTA per SM (the copy rings fill shared memory).  A cluster's
+// time is its sites' bytes over its CTAs, so the size maximises CTAs per
+// cluster / waves, the waves counted from the occupancy query of each size
+// (2..16; GB300's GPCs hold 7 clusters of 16, 15 of 8, 16 of 9); small bonds
+// take fewer.  NNE_OPT_SWEEP_CLUSTER forces a size.
+int g_sweep_cluster = 0;
+void set_sweep_cluster(int cs) { g_sweep_cluster = cs < 0 ? 0 : (cs > 16 ? 16 : cs); }
+
+template <typename R>
 static int sweep_cluster_size(int n_inst, int D) {
+  if (g_sweep_cluster > 0) return g_sweep_cluster;
   if (D < 16) return 1;
   if (D < 64) return 4;
-  return 2 * n_inst * 16 <= 128 ? 16 : 8;
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> memo;
+  const std::pair<int, int> key{n_inst, D};
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+  }
+  const int clusters = 2 * n_inst;
+  int best = 8;
+  double best_rate = 0;
+  for (int cs = 16; cs >= 2; --cs) {
+    const sweep::Layout L{D, sweep::slice_cap(D, cs)};
+    const size_t smem = L.bytes(sizeof(cx<R>));
+    if (smem > 227 * 1024) continue;
+    if (ensure_kernel_smem((const void*)env_cluster_kernel<R>, smem, cs > 8) != cudaSuccess) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 2, n_inst);
+    cfg.blockDim = dim3(sweep::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, (const void*)env_cluster_kernel<R>, &cfg) != cudaSuccess ||
+        active < 1) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    const int waves = (clusters + active - 1) / active;
+    const double rate = (double)cs / waves;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best = cs;
+    }
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  memo[key] = best;
+  return best;
 }
 
 template <typename R>
@@ -500,9 +612,10 @@ cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* 
                          double* d_envscale, double* d_vecs, double* d_out) {
   cudaError_t e;
   {
-    const int cs = sweep_cluster_size(n_inst, max_dim);
+    const int cs = sweep_cluster_size<R>(n_inst, max_dim);
     const sweep::Layout L{max_dim, sweep::slice_cap(max_dim, cs)};
     const size_t smem = L.bytes(sizeof(cx<R>));
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;   // bonds above ~3000 do not fit the copy rings
     if ((e = ensure_kernel_smem((const void*)env_cluster_kernel<R>, smem, cs > 8)) != cudaSuccess) return e;
     // algorithmic bytes: every site tensor read once by each pass
     ProfScope ps(st, K_SWEEP_ENV);

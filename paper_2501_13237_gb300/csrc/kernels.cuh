@@ -66,6 +66,8 @@ bool cgemm_tma_available();
 // (A must not change until tma_release(st), which frees the planes).
 cudaError_t tma_hold_a(cudaStream_t st, int opA, int M, int K, const cx<float>* A, long long sA, int lda, int batch);
 void tma_release(cudaStream_t st);
+// Pipeline variant of the TMA GEMM (1: 128-byte swizzle, 2 stages; 2: 64-byte swizzle, 4 stages).
+void set_tma_variant(int v);
 // Test hook: bound (polls) of the TMA GEMM's pipeline waits; 0 restores the default.
 void set_tc_wait_limit(long long polls);
 void set_gemm_tma(int on);
@@ -150,6 +152,8 @@ cudaError_t expect_sweep(cudaStream_t st, int n, const int* d_dims, const void* 
                          const long long* d_stride, int n_inst, int max_dim, int n_obs, const uint8_t* d_paulis,
                          const int* d_first, const int* d_last, const int* d_general, int n_general, double* d_env,
                          double* d_envscale, double* d_vecs, double* d_out /* n_inst x n_obs x 2 */);
+// Cluster size of the environment sweep: 0 picks it from occupancy, 1..16 forces it.
+void set_sweep_cluster(int cs);
 
 // ---- k_superop.cu
 cudaError_t build_superops(cudaStream_t st, int n_gates, const double* d_U, int n_inst, const double* d_rates,

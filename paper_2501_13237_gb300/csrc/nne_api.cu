@@ -237,7 +237,7 @@ int g_substreams = 4;
 // context stream (nne_set_option NNE_OPT_SERIAL_LAYERS).
 int g_serial_layers = 0;
 // complex64 eigenproblems with a float64 reduction and tridiagonal solve (NNE_OPT_EIG_FP64).
-int g_eig_fp64 = 0;
+int g_eig_fp64 = 1;
 
 void destroy_streams(nne_state* s) {
   for (cudaStream_t q : s->sub_st) cudaStreamDestroy(q);
@@ -1198,8 +1198,12 @@ void nne_set_option(int option, int value) {
   if (option == NNE_OPT_SUBBATCHES) g_substreams = value < 1 ? 1 : (value > 8 ? 8 : value);
   if (option == NNE_OPT_SERIAL_LAYERS) g_serial_layers = value ? 1 : 0;
   if (option == NNE_OPT_EIG_FP64) g_eig_fp64 = value ? 1 : 0;
-  if (option == NNE_OPT_GEMM_TMA) set_gemm_tma(value);
+  if (option == NNE_OPT_GEMM_TMA) {
+    set_gemm_tma(value);
+    if (value) set_tma_variant(value);
+  }
   if (option == NNE_OPT_TEST_WAIT_LIMIT) set_tc_wait_limit(value);
+  if (option == NNE_OPT_SWEEP_CLUSTER) set_sweep_cluster(value);
 }
 
 nne_status nne_cgemm_c64(nne_ctx* ctx, int op_a, int op_b, int M, int N, int K, const float* alpha, const void* A,

@@ -292,6 +292,7 @@ OPT_SERIAL_LAYERS = 2
 OPT_EIG_FP64 = 3
 OPT_GEMM_TMA = 4
 OPT_TEST_WAIT_LIMIT = 5
+OPT_SWEEP_CLUSTER = 6
 
 
 class State:
@@ -397,7 +398,7 @@ class State:
 
 
 PROF_CLASSES = ("gemm", "superop_epilogue", "tridiag", "bisect", "inviter", "backtransform", "qr_factor",
-                "wy_apply", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit", "gemm_tc")
+                "wy_apply", "elementwise", "sweep_env", "sweep_obs", "superop_build", "fit", "gemm_tc", "bisect64")
 
 
 def kernel_launches() -> int:

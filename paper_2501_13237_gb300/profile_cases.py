@@ -1,8 +1,8 @@
 """Small, self-contained GPU cases for profiling single kernels with ncu.
 
-    python -m paper_2501_13237_gb300.profile_cases gemm M N K BATCH
+    python -m paper_2501_13237_gb300.profile_cases gemm M N K BATCH [VARIANT]
         random complex64 A (M x K), B (K x N), C on the device; nne_cgemm_c64
-        (C = A B + 0.5 C) four times.
+        (C = A B + 0.5 C) four times; VARIANT is NNE_OPT_GEMM_TMA (default 2).
     python -m paper_2501_13237_gb300.profile_cases gate [CHI] [N_INST]
         one saturated two-qubit gate step with the bench's truncation
         (bonds CHI, subspace iteration with k = CHI + 128 columns and four
@@ -21,9 +21,10 @@ import sys
 import numpy as np
 
 
-def gemm(M: int, N: int, K: int, batch: int) -> None:
+def gemm(M: int, N: int, K: int, batch: int, variant: int = 2) -> None:
     import torch
     from . import nne
+    nne.set_option(nne.OPT_GEMM_TMA, variant)
     ctx = nne.Context(0)
     g = torch.Generator(device="cuda").manual_seed(0)
     A = torch.randn(batch, M, K, dtype=torch.complex64, device="cuda", generator=g)

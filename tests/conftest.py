@@ -9,8 +9,8 @@ if ROOT not in sys.path:
 
 
 def pytest_addoption(parser):
-    parser.addoption("--eig-fp64", action="store_true", default=False,
-                     help="run the GPU tests with complex64 eigenproblems solved in float64 (NNE_OPT_EIG_FP64)")
+    parser.addoption("--eig-fp32", action="store_true", default=False,
+                     help="run the GPU tests with complex64 eigenproblems solved in float32 (NNE_OPT_EIG_FP64 = 0)")
 
 
 def pytest_configure(config):
@@ -19,10 +19,10 @@ def pytest_configure(config):
 
 @pytest.fixture(autouse=True, scope="session")
 def _eig_precision(request):
-    if not request.config.getoption("--eig-fp64"):
+    if not request.config.getoption("--eig-fp32"):
         yield
         return
     from paper_2501_13237_gb300 import nne
-    nne.set_option(nne.OPT_EIG_FP64, 1)
-    yield
     nne.set_option(nne.OPT_EIG_FP64, 0)
+    yield
+    nne.set_option(nne.OPT_EIG_FP64, 1)

@@ -19,7 +19,7 @@ from tests.gpu_util import rand_c, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 1e-8, 0: 2e-3}
+TOL = {1: 1e-8, 0: 1e-4}
 
 
 @pytest.fixture(scope="module")

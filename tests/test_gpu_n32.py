@@ -20,19 +20,35 @@ def ctx():
     return nne.Context(0)
 
 
-def test_n32_complex64_next_to_complex128(ctx):
-    from paper_2501_13237_gb300 import runner
+_C128 = {}
+
+
+@pytest.mark.parametrize("eig64,tol", [(1, 1e-4), (0, 5e-4)])
+def test_n32_complex64_next_to_complex128(ctx, eig64, tol):
+    """The whole circuit (310 gates x 6 levels) in complex64 against complex128.
+    With the float64 eigensolve (the default) the two agree within the 1e-4
+    budget.  With the float32 eigensolve a reduction error of eps_32 times the
+    largest eigenvalue turns the eigenvectors next to the cut at every gate
+    (by eps_32 ||H|| / gap), and over the circuit the observables drift by a
+    few 1e-4: that mode's bound is 5e-4."""
+    from paper_2501_13237_gb300 import nne, runner
     w = wl.n32()
     rates = w.rate_table()
     paulis = wl.pauli_codes(w.observables, w.n)
-    st, v64, lf64 = runner.emulate(ctx, w.circuit, rates, w.chi, paulis, 0, bits=w.bits())
-    st.close()
-    st, v128, lf128 = runner.emulate(ctx, w.circuit, rates, w.chi, paulis, 1, bits=w.bits())
-    st.close()
+    nne.set_option(nne.OPT_EIG_FP64, eig64)
+    try:
+        st, v64, lf64 = runner.emulate(ctx, w.circuit, rates, w.chi, paulis, 0, bits=w.bits())
+        st.close()
+    finally:
+        nne.set_option(nne.OPT_EIG_FP64, 1)
+    if not _C128:
+        st, v128, lf128 = runner.emulate(ctx, w.circuit, rates, w.chi, paulis, 1, bits=w.bits())
+        st.close()
+        _C128["v"], _C128["lf"] = v128, lf128
+    v128, lf128 = _C128["v"], _C128["lf"]
     assert (lf128 < -1e-4).all()                       # truncation happens
-    # same truncations up to float32 rounding of the Gram eigenproblem
-    assert np.abs(v64.real - v128.real).max() < 1e-3
-    assert np.abs(lf64 - lf128).max() < 1e-3 * np.abs(lf128).max()
+    assert np.abs(v64.real - v128.real).max() < tol, np.abs(v64.real - v128.real).max()
+    assert np.abs(lf64 - lf128).max() < tol * np.abs(lf128).max(), np.abs(lf64 - lf128).max()
 
 
 _ORACLE = {}
@@ -47,7 +63,7 @@ def _prefix():
     return w, c, rates, _ORACLE["refs"]
 
 
-@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 3e-4)])
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 1e-4)])
 def test_n32_prefix_vs_oracle(ctx, dtype, tol):
     from paper_2501_13237_gb300 import runner
     w, c, rates, refs = _prefix()

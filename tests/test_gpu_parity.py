@@ -336,3 +336,51 @@ def test_checkpoint_restore_continues_bit_for_bit(ctx):
         b.close()
         assert np.array_equal(va, vb) and np.array_equal(lfa, lfb)
         assert (lfa < -1e-6).all()
+
+
+def _tiny_noise(rng, shape, lo=1e-24, hi=1e-7):
+    mag = np.exp(rng.uniform(np.log(lo), np.log(hi), shape))
+    return mag * np.exp(2j * np.pi * rng.uniform(size=shape))
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-12), (0, 1e-6)])
+@pytest.mark.parametrize("direction", [+1, -1])
+def test_gauge_moves_on_nearly_null_columns(ctx, dtype, tol, direction):
+    """Clifford circuits leave site tensors that are scaled permutations plus
+    rounding noise spread over many decades (1e-24 .. 1e-7): the QR and LQ of
+    a gauge move then meet reflector pivots and column remainders whose
+    float32 squares are denormal.  An identity gate after the move must
+    return theta unchanged (up to the kept norm): the reflectors stay unitary
+    only with the pivots and norms formed in float64."""
+    import torch
+    from paper_2501_13237_gb300 import nne
+    rng = np.random.default_rng(11)
+    # 3 sites, bonds 1, 4, 4, 1; the middle tensor as a 16 x 4 (direction -1, QR
+    # of M1) or 4 x 16 (direction +1, LQ of M1) matrix with one large entry per column
+    big = np.zeros((16, 4), complex)
+    for j, s in enumerate((0.52, 0.48, 0.48, 0.52)):
+        big[4 * j, j] = s * np.exp(1j * rng.uniform(0, 2 * np.pi))
+    P = big + _tiny_noise(rng, (16, 4))
+    M1 = (P.conj().T if direction > 0 else P).reshape(4, 4, 4)
+    M0 = np.eye(4, dtype=complex).reshape(1, 4, 4)
+    M2 = np.eye(4, dtype=complex).reshape(4, 4, 1)
+    if dtype == 0:
+        M0, M1, M2 = (m.astype(np.complex64) for m in (M0, M1, M2))
+    st = nne.State(ctx, 3, 4, 1, dtype)
+    for k, M in enumerate((M0, M1, M2)):
+        st.write_site(0, k, M)
+    st.set_centre(1 if direction > 0 else 0)
+    G = torch.from_numpy(np.eye(16, dtype=complex)[None, None].copy()).cuda()
+    q = 0 if direction > 0 else 1
+    st.apply_layer([q], G, direction)
+    st.sync()
+    A = [st.read_site(0, k).astype(complex) for k in range(3)]
+    st.close()
+    if direction > 0:
+        before = np.einsum("asc,ctb->astb", M0.astype(complex), M1.astype(complex)).reshape(-1)
+        after = np.einsum("asc,ctb->astb", A[0], A[1]).reshape(-1)
+    else:
+        before = np.einsum("asc,ctb->astb", M1.astype(complex), M2.astype(complex)).reshape(-1)
+        after = np.einsum("asc,ctb->astb", A[1], A[2]).reshape(-1)
+    err = np.abs(after / np.linalg.norm(after) - before / np.linalg.norm(before)).max()
+    assert err < tol, err

@@ -29,7 +29,7 @@ def _workloads():
     return [a, b, c]
 
 
-@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 2e-4)])
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-8), (0, 1e-4)])
 def test_server_matches_direct_and_oracle(ctx, dtype, tol):
     from paper_2501_13237_gb300 import nne, runner
     ws = _workloads()
@@ -157,7 +157,7 @@ def test_batch_subsample_vs_oracle(ctx):
     for w, r in zip(ws, res):
         paulis = wl.pauli_codes(w.observables, w.n)
         ref = mps.run(w.circuit, w.rate_table()[0], w.chi, bits=w.bits())
-        assert np.abs(r["values"][0] - ref.expect_codes(paulis).real).max() < 2e-4
+        assert np.abs(r["values"][0] - ref.expect_codes(paulis).real).max() < 1e-4
         # log F sums one complex64-rounded log f per gate (about 1e-5 each): the bound grows with the gates
         assert abs(r["log_fid"][0] - ref.log_fid) < 2e-5 * w.circuit.n_gates
         assert r["gate_steps"] == w.circuit.n_gates * len(w.lambdas)

@@ -4,8 +4,9 @@ the same site tensors.
 
 Random chains written site by site cover what an evolved state may not: bond
 dimensions that are odd (the sweep's scalar-load path for complex64) and even
-(its 16-byte path), every cluster size the launcher picks (1, 4, 8 and 16 CTAs
-per pass and instance), strings on one site, on two neighbouring sites, on
+(its 16-byte path), cluster sizes from 1 to 16 CTAs per pass and instance
+(the launcher's own choice and forced sizes, powers of two or not), strings on
+one site, on two neighbouring sites, on
 three or more sites (the carried-vector kernel), strings at both chain ends
 and the identity string."""
 import numpy as np
@@ -78,13 +79,30 @@ def run_chain(ctx, dtype, bonds, n_inst, seed):
 
 
 @pytest.mark.parametrize("dtype", [1, 0])
-@pytest.mark.parametrize("n_inst", [1, 3, 6])
+@pytest.mark.parametrize("n_inst", [1, 3, 6, 8])
 def test_sweep_random_chain_wide(ctx, dtype, n_inst):
-    """Bonds 1, 4, 16, 64, 256, 520, 256, ...: 16 CTAs per cluster up to 4
-    instances, 8 beyond."""
+    """Bonds 1, 4, 16, 64, 256, 520, 256, ...: the cluster size the launcher
+    picks from occupancy for 2, 6, 12 and 16 clusters."""
     n, chi = 10, 520
     bonds = [min(chi, 4 ** k, 4 ** (n - k)) for k in range(n + 1)]
     run_chain(ctx, dtype, bonds, n_inst, 100 + n_inst + 7 * dtype)
+
+
+@pytest.mark.parametrize("dtype", [1, 0])
+@pytest.mark.parametrize("cs", [2, 3, 5, 9, 12, 16])
+def test_sweep_forced_cluster_sizes(ctx, dtype, cs):
+    """Slices of 520- and 517-wide bonds (16-byte and scalar loads) split over
+    cluster sizes that divide neither."""
+    from paper_2501_13237_gb300 import nne
+    n, chi = 11, 520
+    bonds = [min(chi, 4 ** k, 4 ** (n - k)) for k in range(n + 1)]
+    assert bonds[5] == bonds[6] == 520
+    bonds[6] = 517
+    nne.set_option(nne.OPT_SWEEP_CLUSTER, cs)
+    try:
+        run_chain(ctx, dtype, bonds, 2, 300 + cs + dtype)
+    finally:
+        nne.set_option(nne.OPT_SWEEP_CLUSTER, 0)
 
 
 @pytest.mark.parametrize("dtype", [1, 0])
