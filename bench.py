@@ -399,6 +399,8 @@ def roofline(dominant, prof, pk, meas):
     name, (t_ms, count, work) = dominant
     if count == 0 or t_ms <= 0:
         return None
+    # traffic: no ncu capture of this build's launch mix for the class (the GEMM class mixes ~20
+    # shapes per gate; per-shape DRAM counters are in profiles/), so null
     out = {"kernel": name, "launches": count, "avg_launch_ms": t_ms / count, "traffic": None}
     achieved = work / (t_ms / 1e3) / 1e12 if work > 0 else None
     if name == "gemm_tc" and achieved is not None:

@@ -651,26 +651,35 @@ __global__ void __launch_bounds__(512) tridiag_df_kernel(float4* Hb, long long s
       wdf[t] = make_float4(rh, rl, ih, il);
     }
     __syncthreads();
-    // A <- A - v w^H - w v^H on the lower triangle of own rows
+    // A <- A - v w^H - w v^H on the lower triangle of own rows (U entries in flight per lane)
     for (int t = gw; t < m; t += GW) {
       float4* row = H + (long long)(j + 1 + t) * n + (j + 1);
       const float4 vt = vdf[t], wt = wdf[t];
-      for (int k = lane; k <= t; k += 32) {
-        float4 a = row[k];
-        const float4 wk = wdf[k], vk = vdf[k];
-        // re: - (vt.re wk.re + vt.im wk.im + wt.re vk.re + wt.im vk.im)
-        df_mac(a.x, a.y, -vt.x, -vt.y, wk.x, wk.y);
-        df_mac(a.x, a.y, -vt.z, -vt.w, wk.z, wk.w);
-        df_mac(a.x, a.y, -wt.x, -wt.y, vk.x, vk.y);
-        df_mac(a.x, a.y, -wt.z, -wt.w, vk.z, vk.w);
-        // im: - (vt.im wk.re - vt.re wk.im + wt.im vk.re - wt.re vk.im)
-        df_mac(a.z, a.w, -vt.z, -vt.w, wk.x, wk.y);
-        df_mac(a.z, a.w, vt.x, vt.y, wk.z, wk.w);
-        df_mac(a.z, a.w, -wt.z, -wt.w, vk.x, vk.y);
-        df_mac(a.z, a.w, wt.x, wt.y, vk.z, vk.w);
-        df_norm(a.x, a.y);
-        df_norm(a.z, a.w);
-        row[k] = a;
+      for (int k0 = lane; k0 <= t; k0 += 32 * U) {
+        float4 a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k0 + 32 * u <= t) a[u] = row[k0 + 32 * u];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + 32 * u;
+          if (k > t) break;
+          const float4 wk = wdf[k], vk = vdf[k];
+          float4 b = a[u];
+          // re: - (vt.re wk.re + vt.im wk.im + wt.re vk.re + wt.im vk.im)
+          df_mac(b.x, b.y, -vt.x, -vt.y, wk.x, wk.y);
+          df_mac(b.x, b.y, -vt.z, -vt.w, wk.z, wk.w);
+          df_mac(b.x, b.y, -wt.x, -wt.y, vk.x, vk.y);
+          df_mac(b.x, b.y, -wt.z, -wt.w, vk.z, vk.w);
+          // im: - (vt.im wk.re - vt.re wk.im + wt.im vk.re - wt.re vk.im)
+          df_mac(b.z, b.w, -vt.z, -vt.w, wk.x, wk.y);
+          df_mac(b.z, b.w, vt.x, vt.y, wk.z, wk.w);
+          df_mac(b.z, b.w, -wt.z, -wt.w, vk.x, vk.y);
+          df_mac(b.z, b.w, wt.x, wt.y, vk.z, vk.w);
+          df_norm(b.x, b.y);
+          df_norm(b.z, b.w);
+          row[k] = b;
+        }
       }
     }
     __threadfence();
@@ -726,10 +735,11 @@ static int cluster_size_for(int n) { return n >= 512 ? 8 : (n >= 128 ? 4 : (n >=
 // 13-16 single-SM CTAs).  The size depends on nothing but the kernel, so
 // results do not depend on how instances are batched.
 constexpr size_t TRIDIAG64_SMEM = 120 * 1024;
-// double-float reduction launch (measured at n = 640, 2 matrices: 256 threads and one load in flight
-// per lane 26.2 ms; 4 loads 27.0; 512 threads with 2 or 4 loads 26.7-26.9)
+// double-float reduction launch: 256 threads, TRIDIAG_DF_UNROLL loads in flight per lane in the
+// product A v and the rank-2 update (its loads wait on L2: ncu shows long-scoreboard stalls and
+// 1.6 % L2 throughput with one load per lane)
 constexpr int TRIDIAG_DF_THREADS = 256;
-constexpr int TRIDIAG_DF_UNROLL = 1;
+constexpr int TRIDIAG_DF_UNROLL = 4;
 static int tridiag64_cluster_size(const void* kernel) {
   static std::mutex mu;
   static std::map<const void*, int> memo;

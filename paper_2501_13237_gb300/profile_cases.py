@@ -3,10 +3,12 @@
     python -m paper_2501_13237_gb300.profile_cases gemm M N K BATCH [VARIANT]
         random complex64 A (M x K), B (K x N), C on the device; nne_cgemm_c64
         (C = A B + 0.5 C) four times; VARIANT is NNE_OPT_GEMM_TMA (default 2).
-    python -m paper_2501_13237_gb300.profile_cases gate [CHI] [N_INST]
+    python -m paper_2501_13237_gb300.profile_cases gate [CHI] [N_INST] [SERIAL]
         one saturated two-qubit gate step with the bench's truncation
         (bonds CHI, subspace iteration with k = CHI + 128 columns and four
-        power iterations, Rayleigh-Ritz) on N_INST instances.
+        power iterations, Rayleigh-Ritz) on N_INST instances; SERIAL = 1 runs
+        all instances as one batch on one stream (NNE_OPT_SERIAL_LAYERS), the
+        launch mix of the bench's profiled step.
     python -m paper_2501_13237_gb300.profile_cases sweep N CHI N_INST
         a chain of N sites with every bond at CHI (random complex64 site
         tensors, N_INST instances) and one expectation sweep over every
@@ -35,10 +37,11 @@ def gemm(M: int, N: int, K: int, batch: int, variant: int = 2) -> None:
     torch.cuda.synchronize()
 
 
-def gate(chi: int = 512, n_inst: int = 8) -> None:
+def gate(chi: int = 512, n_inst: int = 8, serial: int = 0) -> None:
     import workloads as wl
     from . import nne
     n, q = 14, 5
+    nne.set_option(nne.OPT_SERIAL_LAYERS, serial)
     ctx = nne.Context(0)
     st = nne.State(ctx, n, chi, n_inst, nne.C64, nne.TRUNC_RSVD)
     st.set_sketch(wl.gaussian_sketch(4 * chi, chi + 128, 1).astype(np.complex64), 4)
